@@ -1,0 +1,307 @@
+/*
+ * Oracle for maximum cardinality bipartite matching -- TEST INFRASTRUCTURE.
+ *
+ * Plain, sequential, obviously correct CPU code that the tests, the
+ * benchmark's CPU baseline and the package's smoke check compare the CUDA path
+ * against.  It shares no code with the CUDA path and the product never calls
+ * it.  Only tests/, __graft_entry__.smoke() and bench.py's CPU baseline load
+ * this library.
+ *
+ * Problem (Deveci, Kaya, Ucar, Catalyurek, arXiv 1303.1379, Section 2): a
+ * bipartite graph with row and column vertices, stored by columns
+ * (Section 3: cxadj/cadj, here col_ptr[nc+1]/row_idx[nnz]); a matching is a
+ * set of edges with no shared vertex, stored as rmatch[r] = c, cmatch[c] = r,
+ * -1 for unmatched (Section 3).  The method reaches a maximum matching, whose
+ * size nu(G) has a plain definition; this file computes it independently:
+ *
+ *   orc_greedy          the "cheap matching" initialisation of Section 4 in
+ *                       its simplest form: columns in order, each takes the
+ *                       first unmatched row of its adjacency list.
+ *   orc_hopcroft_karp   Hopcroft-Karp (cited in Sections 1-2 as HK, the
+ *                       O(sqrt(n) tau) algorithm): phases of a BFS layering
+ *                       from all free columns up to the first layer that
+ *                       touches a free row, then DFS in the layered graph for
+ *                       a maximal set of vertex-disjoint shortest augmenting
+ *                       paths, each applied as M <- M xor E(P) (Section 2).
+ *   orc_validate        the definition of a matching (Section 2).
+ *   orc_konig           a Koenig vertex-cover certificate of maximality: the
+ *                       alternating reachability set Z from the free columns
+ *                       must touch no free row (Berge, Section 2), and the
+ *                       cover (C \ Z_C) u Z_R must cover every edge and have
+ *                       exactly |M| vertices.
+ *   orc_bfs_levels      the alternating BFS distance of every column from the
+ *                       free columns for a fixed matching -- what one full
+ *                       GPUBFS pass (Algorithm 2, APFB without the early break
+ *                       of Algorithm 1) assigns to bfs_array, offset by L0 --
+ *                       and the set of free rows that the BFS reaches.
+ *   orc_hk_batch        orc_hopcroft_karp over many graphs of a batch.
+ *
+ * All indices are int32 and the arithmetic is exact integer.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_EXPORT __attribute__((visibility("default")))
+
+enum {
+    ORC_OK = 0,
+    ORC_BAD_ARG = -1,
+    ORC_NOMEM = -2,
+    ORC_BAD_INDEX = -3,      /* a match entry outside [-1, n)             */
+    ORC_NOT_INVERSE = -4,    /* rmatch and cmatch disagree                */
+    ORC_NOT_EDGE = -5,       /* a matched pair is not an edge             */
+    ORC_AUGMENTABLE = -6,    /* an augmenting path exists: not maximum     */
+    ORC_UNCOVERED = -7,      /* an edge misses the Koenig cover            */
+    ORC_COVER_SIZE = -8      /* cover size differs from |M|                */
+};
+
+/* CSR sanity: col_ptr starts at 0, never decreases, ends at nnz; rows in range. */
+ORC_EXPORT int orc_csr_check(int32_t nr, int32_t nc, int64_t nnz, const int32_t *cp,
+                             const int32_t *ri) {
+    if (nr < 0 || nc < 0 || nnz < 0) return ORC_BAD_ARG;
+    if (cp[0] != 0 || (int64_t)cp[nc] != nnz) return ORC_BAD_ARG;
+    for (int32_t c = 0; c < nc; ++c)
+        if (cp[c + 1] < cp[c]) return ORC_BAD_ARG;
+    for (int64_t e = 0; e < nnz; ++e)
+        if (ri[e] < 0 || ri[e] >= nr) return ORC_BAD_INDEX;
+    return ORC_OK;
+}
+
+ORC_EXPORT int64_t orc_greedy(int32_t nr, int32_t nc, const int32_t *cp, const int32_t *ri,
+                              int32_t *rmatch, int32_t *cmatch) {
+    int64_t card = 0;
+    for (int32_t r = 0; r < nr; ++r) rmatch[r] = -1;
+    for (int32_t c = 0; c < nc; ++c) {
+        cmatch[c] = -1;
+        for (int32_t e = cp[c]; e < cp[c + 1]; ++e) {
+            int32_t r = ri[e];
+            if (rmatch[r] == -1) {
+                rmatch[r] = c;
+                cmatch[c] = r;
+                ++card;
+                break;
+            }
+        }
+    }
+    return card;
+}
+
+/* Is row r adjacent to column c? (linear scan: the oracle favours clarity) */
+static int has_edge(const int32_t *cp, const int32_t *ri, int32_t c, int32_t r) {
+    for (int32_t e = cp[c]; e < cp[c + 1]; ++e)
+        if (ri[e] == r) return 1;
+    return 0;
+}
+
+ORC_EXPORT int orc_validate(int32_t nr, int32_t nc, const int32_t *cp, const int32_t *ri,
+                            const int32_t *rmatch, const int32_t *cmatch, int64_t *card_out) {
+    int64_t rows = 0, cols = 0;
+    for (int32_t r = 0; r < nr; ++r) {
+        int32_t c = rmatch[r];
+        if (c == -1) continue;
+        if (c < 0 || c >= nc) return ORC_BAD_INDEX;
+        if (cmatch[c] != r) return ORC_NOT_INVERSE;
+        if (!has_edge(cp, ri, c, r)) return ORC_NOT_EDGE;
+        ++rows;
+    }
+    for (int32_t c = 0; c < nc; ++c) {
+        int32_t r = cmatch[c];
+        if (r == -1) continue;
+        if (r < 0 || r >= nr) return ORC_BAD_INDEX;
+        if (rmatch[r] != c) return ORC_NOT_INVERSE;
+        ++cols;
+    }
+    if (rows != cols) return ORC_NOT_INVERSE;
+    if (card_out) *card_out = rows;
+    return ORC_OK;
+}
+
+/* Hopcroft-Karp from the given (valid) initial matching.  Returns |M| or a
+ * negative error; *phases_out gets the number of phases that augmented. */
+ORC_EXPORT int64_t orc_hopcroft_karp(int32_t nr, int32_t nc, const int32_t *cp, const int32_t *ri,
+                                     int32_t *rmatch, int32_t *cmatch, int64_t *phases_out) {
+    const int32_t INF = INT32_MAX;
+    int64_t card;
+    int rc = orc_validate(nr, nc, cp, ri, rmatch, cmatch, &card);
+    if (rc != ORC_OK) return rc;
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nc ? nc : 1));
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nc ? nc : 1));
+    int32_t *next_edge = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nc ? nc : 1));
+    int32_t *stack_col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nc + 1));
+    int32_t *stack_row = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nc + 1));
+    if (!dist || !queue || !next_edge || !stack_col || !stack_row) {
+        free(dist); free(queue); free(next_edge); free(stack_col); free(stack_row);
+        return ORC_NOMEM;
+    }
+    int64_t phases = 0;
+    for (;;) {
+        /* BFS layering from every free column. */
+        int32_t head = 0, tail = 0;
+        for (int32_t c = 0; c < nc; ++c) {
+            if (cmatch[c] == -1) { dist[c] = 0; queue[tail++] = c; }
+            else dist[c] = INF;
+        }
+        int32_t limit = INF; /* layer of the columns that touch a free row */
+        while (head < tail) {
+            int32_t c = queue[head++];
+            if (dist[c] >= limit) continue; /* only layers below the first free row expand */
+            for (int32_t e = cp[c]; e < cp[c + 1]; ++e) {
+                int32_t r = ri[e];
+                int32_t c2 = rmatch[r];
+                if (c2 == -1) {
+                    if (limit == INF) limit = dist[c];
+                } else if (dist[c2] == INF) {
+                    dist[c2] = dist[c] + 1;
+                    queue[tail++] = c2;
+                }
+            }
+        }
+        if (limit == INF) break; /* no augmenting path: maximum (Berge) */
+        ++phases;
+        /* DFS from each free column inside the layered graph. */
+        for (int32_t c = 0; c < nc; ++c) next_edge[c] = cp[c];
+        for (int32_t root = 0; root < nc; ++root) {
+            if (cmatch[root] != -1 || dist[root] != 0) continue;
+            int32_t sp = 0;
+            stack_col[0] = root;
+            while (sp >= 0) {
+                int32_t c = stack_col[sp];
+                if (next_edge[c] == cp[c + 1]) { /* exhausted: dead end */
+                    dist[c] = INF;
+                    --sp;
+                    continue;
+                }
+                int32_t r = ri[next_edge[c]++];
+                int32_t c2 = rmatch[r];
+                if (c2 == -1) {
+                    if (dist[c] != limit) continue;
+                    stack_row[sp] = r;
+                    /* M <- M xor E(P) along the stack */
+                    for (int32_t k = sp; k >= 0; --k) {
+                        rmatch[stack_row[k]] = stack_col[k];
+                        cmatch[stack_col[k]] = stack_row[k];
+                    }
+                    ++card;
+                    break;
+                }
+                if (dist[c2] != INF && dist[c2] == dist[c] + 1 && dist[c2] <= limit) {
+                    stack_row[sp] = r;
+                    stack_col[++sp] = c2;
+                }
+            }
+        }
+    }
+    free(dist); free(queue); free(next_edge); free(stack_col); free(stack_row);
+    if (phases_out) *phases_out = phases;
+    return card;
+}
+
+/* Koenig certificate.  Returns ORC_OK and *cover_out = |K| when the matching
+ * is valid and maximum; an error code otherwise. */
+ORC_EXPORT int orc_konig(int32_t nr, int32_t nc, const int32_t *cp, const int32_t *ri,
+                         const int32_t *rmatch, const int32_t *cmatch, int64_t *cover_out) {
+    int64_t card;
+    int rc = orc_validate(nr, nc, cp, ri, rmatch, cmatch, &card);
+    if (rc != ORC_OK) return rc;
+    uint8_t *zc = (uint8_t *)calloc((size_t)nc + 1, 1);
+    uint8_t *zr = (uint8_t *)calloc((size_t)nr + 1, 1);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nc ? nc : 1));
+    if (!zc || !zr || !queue) { free(zc); free(zr); free(queue); return ORC_NOMEM; }
+    int32_t head = 0, tail = 0;
+    for (int32_t c = 0; c < nc; ++c)
+        if (cmatch[c] == -1) { zc[c] = 1; queue[tail++] = c; }
+    rc = ORC_OK;
+    while (head < tail && rc == ORC_OK) {
+        int32_t c = queue[head++];
+        for (int32_t e = cp[c]; e < cp[c + 1]; ++e) {
+            int32_t r = ri[e];
+            if (zr[r]) continue;
+            zr[r] = 1;
+            int32_t c2 = rmatch[r];
+            if (c2 == -1) { rc = ORC_AUGMENTABLE; break; }
+            if (!zc[c2]) { zc[c2] = 1; queue[tail++] = c2; }
+        }
+    }
+    if (rc == ORC_OK) {
+        int64_t size = 0;
+        for (int32_t c = 0; c < nc; ++c) size += !zc[c];
+        for (int32_t r = 0; r < nr; ++r) size += zr[r];
+        for (int32_t c = 0; c < nc && rc == ORC_OK; ++c) {
+            if (!zc[c]) continue; /* column in the cover covers its edges */
+            for (int32_t e = cp[c]; e < cp[c + 1]; ++e)
+                if (!zr[ri[e]]) { rc = ORC_UNCOVERED; break; }
+        }
+        if (rc == ORC_OK && size != card) rc = ORC_COVER_SIZE;
+        if (cover_out) *cover_out = size;
+    }
+    free(zc); free(zr); free(queue);
+    return rc;
+}
+
+/* Alternating BFS distances for a fixed matching.  level[c] = L0 + distance
+ * for every column reachable from a free column (free columns have L0),
+ * L0 - 1 for the others.  reached_free_row[r] = 1 for every unmatched row
+ * adjacent to a reached column.  Returns the number of such rows. */
+ORC_EXPORT int64_t orc_bfs_levels(int32_t nr, int32_t nc, const int32_t *cp, const int32_t *ri,
+                                  const int32_t *rmatch, const int32_t *cmatch, int32_t L0,
+                                  int32_t *level, uint8_t *reached_free_row) {
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nc ? nc : 1));
+    if (!queue) return ORC_NOMEM;
+    memset(reached_free_row, 0, (size_t)nr);
+    int32_t head = 0, tail = 0;
+    for (int32_t c = 0; c < nc; ++c) {
+        if (cmatch[c] == -1) { level[c] = L0; queue[tail++] = c; }
+        else level[c] = L0 - 1;
+    }
+    int64_t found = 0;
+    while (head < tail) {
+        int32_t c = queue[head++];
+        for (int32_t e = cp[c]; e < cp[c + 1]; ++e) {
+            int32_t r = ri[e];
+            int32_t c2 = rmatch[r];
+            if (c2 == -1) {
+                if (!reached_free_row[r]) { reached_free_row[r] = 1; ++found; }
+            } else if (level[c2] == L0 - 1) {
+                level[c2] = level[c] + 1;
+                queue[tail++] = c2;
+            }
+        }
+    }
+    free(queue);
+    return found;
+}
+
+/* Hopcroft-Karp over a batch (graph k: local col_ptr at col_ptr + col_off[k] + k,
+ * rows at row_idx + edge_off[k], matching slices at row_off[k] / col_off[k]).
+ * Graphs run in parallel when OpenMP is available; each graph is sequential. */
+ORC_EXPORT int orc_hk_batch(int32_t n_graphs, const int32_t *nr, const int32_t *nc,
+                            const int64_t *row_off, const int64_t *col_off,
+                            const int64_t *edge_off, const int32_t *col_ptr,
+                            const int32_t *row_idx, int32_t *rmatch, int32_t *cmatch,
+                            int32_t greedy_first, int64_t *card_out) {
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int32_t k = 0; k < n_graphs; ++k) {
+        const int32_t *cp = col_ptr + col_off[k] + k;
+        const int32_t *ri = row_idx + edge_off[k];
+        int32_t *rm = rmatch + row_off[k];
+        int32_t *cm = cmatch + col_off[k];
+        if (greedy_first) orc_greedy(nr[k], nc[k], cp, ri, rm, cm);
+        int64_t card = orc_hopcroft_karp(nr[k], nc[k], cp, ri, rm, cm, NULL);
+        if (card < 0) bad = 1;
+        card_out[k] = card;
+    }
+    return bad ? ORC_BAD_ARG : ORC_OK;
+}
+
+ORC_EXPORT int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
