@@ -1,0 +1,429 @@
+"""Benchmark: time to a maximum matching on one GB300 (and N replicas).
+
+Workload (default): R-MAT scale 21 -- 2^21 rows x 2^21 columns, 2^25 samples
+with quadrant probabilities a=.57 b=.19 c=.19 d=.05, duplicates removed
+(32,416,121 edges), seed 1 -- matched from a greedy initial matching, the
+setting in which Section 4 of arXiv 1303.1379 times its GPU algorithm
+(kron_g500-logn21 is the paper's instance of this shape).
+
+A step = install the saved initial matching + bm_match (every phase of
+Algorithm 1 until no augmenting path remains).  The initial matching comes
+from the GPU cheap-matching kernel once, before timing, as the paper excludes
+initialisation from its times.  L2 is flushed (256 MB write) before every step,
+outside the timed events.
+
+Printed JSON line: value = GTEPS = edges / time-to-maximum-matching summed
+over ranks (replicas), ms_per_step = mean device time of a step (max over
+ranks), e2e = the same through bm_match_host with pinned host buffers
+(CSR + initial matching up, matching down, inside the timed region),
+roofline = algorithmic bytes of the persistent matching kernel / its
+duration against the measured HBM copy peak, cpu_baseline = the oracle
+(Hopcroft-Karp from the oracle's greedy) on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--workload rmat21|stencil2000|uniform10k]
+Under torchrun each rank runs one replica on its own GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "rmat21": "R-MAT scale 21 (2^21 x 2^21), 2^25 samples a=.57 b=.19 c=.19 d=.05, duplicates "
+              "removed, int32 CSR, greedy initial matching, seed 1",
+    "stencil2000": "5-point stencil 2000x2000 (4M x 4M), 400,000 diagonals and 5% of off-diagonals "
+                   "dropped, int32 CSR, greedy initial matching, seed 2",
+    "uniform10k": "uniform 10,000 x 10,000, column degree U{1..8}, int32 CSR, empty initial "
+                  "matching, seed 0",
+}
+METRIC = "ms to max matching, GTEPS and % HBM roofline; batched graphs/s vs one-by-one"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat21", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("paper_1303_1379_gb300/csrc/bmatch.cu", "paper_1303_1379_gb300/csrc/bm_device.cuh"):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it
+    was taken on the current sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("source_hash") == source_hash():
+            return d.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def algorithmic_bytes(st: dict, nr: int, nc: int, wr: bool) -> int:
+    """Bytes the method must move per bm_match launch (4-byte words, each
+    counted once where it is read or written), from the launch's counters:
+
+    per phase  InitBfsArray: cmatch read, level write (+ root write) per column,
+               rmatch[cmatch[c]] check per matched column, a queue push per free one
+    per level  per frontier column: queue read, col_ptr pair (+ root and
+               level[root]); per edge: row_idx and rmatch[row]; per edge to a
+               matched row: level[column]; per inserted column: level CAS, pred,
+               queue push (+ root); per endpoint: rmatch CAS, pred, list push
+               (+ root slot)
+    Alternate  per endpoint: list read; per step: pred, cmatch, pred check,
+               cmatch and rmatch writes
+    Fix        rmatch per row, cmatch[rmatch[r]] per matched row
+    """
+    phases = st["phases"]
+    card = st["final_card"]
+    init = phases * (nc * (8 + (4 if wr else 0)) + 4 * nc)
+    frontier = st["columns_expanded"] * (12 + (8 if wr else 0))
+    edges = st["edges_scanned"] * 8 + st["edges_to_matched"] * 4
+    ins = st["inserted"] * (12 + (4 if wr else 0))
+    ends = st["endpoints"] * (12 + (4 if wr else 0))
+    alt = st["endpoints"] * 4 + st["alternate_steps"] * 20
+    fix = max(phases - 1, 0) * (4 * nr + 4 * card)
+    return int(init + frontier + edges + ins + ends + alt + fix)
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle reasons, sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_workload(name):
+    from paper_1303_1379_gb300 import synth
+    return synth.workload(name)
+
+
+def golden_max(name):
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "workloads.txt")) as f:
+            for line in f:
+                t = line.split("#")[0].split()
+                if t and t[0] == name:
+                    return int(dict(kv.split("=") for kv in t[1:])["max"])
+    except Exception:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    """The oracle (sequential Hopcroft-Karp from the oracle's greedy start) on
+    the host cores, timed per step on the same workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    g = load_workload(args.workload)
+    empty = args.workload == "uniform10k"
+    if empty:
+        rm0, cm0 = oracle.empty_matching(g.n_rows, g.n_cols)
+    else:
+        rm0, cm0, _ = oracle.greedy(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+    times = []
+    card = None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, _, card, _ = oracle.hopcroft_karp(g.n_rows, g.n_cols, g.col_ptr, g.row_idx, rm0, cm0)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    t = statistics.mean(times)
+    gteps = g.nnz / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gteps, "unit": "GTEPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "nnz": g.nnz,
+                   "max_matching": card},
+        "cpu_baseline": {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": f"whole {args.workload} graph, Hopcroft-Karp from the oracle's "
+                                   f"{'empty' if empty else 'greedy'} start, {args.steps} runs"},
+        "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1303_1379_gb300 import bmatch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    g = load_workload(args.workload)
+    nr, nc, nnz = g.n_rows, g.n_cols, g.nnz
+    stream = torch.cuda.current_stream()
+    cp = torch.from_numpy(g.col_ptr).to(dev)
+    ri = torch.from_numpy(g.row_idx).to(dev)
+    m = bmatch.Matcher(nr, nc, nnz, cp, ri, stream=stream.cuda_stream)
+    wr = m.options.bfs == bmatch.BM_GPUBFS_WR
+
+    # initial matching (untimed, as in the paper): GPU cheap matching, saved
+    empty = args.workload == "uniform10k"
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    greedy_card = 0 if empty else m.greedy()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    greedy_ms = t0.elapsed_time(t1)
+    rm0 = torch.empty(nr, dtype=torch.int32, device=dev)
+    cm0 = torch.empty(nc, dtype=torch.int32, device=dev)
+    m.get_matching(rm0, cm0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        m.set_matching(rm0, cm0)
+        return m.match()
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        res = step()
+    want = golden_max(args.workload)
+    if want is not None and res.card != want:
+        raise SystemExit(f"wrong |M|: {res.card} != {want}")
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device() if world == 1 else local)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    kernel_ms, stats = [], []
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i)
+        evs[i][0].record(stream)
+        res = step()
+        evs[i][1].record(stream)
+        stats.append(res.stats)
+        kernel_ms.append(res.stats["kernel_ns"] / 1e6)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = statistics.mean(step_ms)
+    match_ms = statistics.mean(kernel_ms)
+    if world > 1:
+        t = torch.tensor([ms, match_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, match_ms = float(t[0]), float(t[1])
+    gteps = world * nnz / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (the persistent matching launch)
+    peak, peak_kind = measured_peaks()
+    st0 = stats[-1]
+    alg_bytes = statistics.mean(algorithmic_bytes(s, nr, nc, wr) for s in stats)
+    achieved = alg_bytes / (match_ms * 1e-3) / 1e9
+    traffic = ncu_traffic("k_match", args.workload)
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        hm = bmatch.Matcher(nr, nc, nnz, None, None, stream=stream.cuda_stream)
+        h_cp = torch.from_numpy(g.col_ptr).pin_memory()
+        h_ri = torch.from_numpy(g.row_idx).pin_memory()
+        h_rm0 = rm0.cpu().pin_memory()
+        h_cm0 = cm0.cpu().pin_memory()
+        h_rm = torch.empty_like(h_rm0).pin_memory()
+        h_cm = torch.empty_like(h_cm0).pin_memory()
+        e_ms = []
+        for i in range(args.warmup + args.steps):
+            h_rm.copy_(h_rm0)
+            h_cm.copy_(h_cm0)
+            flush.fill_(i)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = hm.match_host(h_cp, h_ri, h_rm, h_cm)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                e_ms.append(a.elapsed_time(b))
+        assert r.card == res.card
+        hm.close()
+        em = statistics.mean(e_ms)
+        if world > 1:
+            t = torch.tensor([em], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            em = float(t[0])
+        e2e = {"value": world * nnz / (em * 1e-3) / 1e9, "unit": "GTEPS",
+               "ms_per_step": em,
+               "h2d_bytes_per_step": 4 * (nc + 1 + nnz + nr + nc),
+               "d2h_bytes_per_step": 4 * (nr + nc)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        if empty:
+            orm, ocm = oracle.empty_matching(nr, nc)
+        else:
+            orm, ocm, _ = oracle.greedy(nr, nc, g.col_ptr, g.row_idx)
+        ts = []
+        budget = 20.0
+        t_all = time.perf_counter()
+        while not ts or (len(ts) < 3 and time.perf_counter() - t_all < budget):
+            a = time.perf_counter()
+            _, _, ocard, _ = oracle.hopcroft_karp(nr, nc, g.col_ptr, g.row_idx, orm, ocm)
+            ts.append(time.perf_counter() - a)
+        assert ocard == res.card, (ocard, res.card)
+        tmed = statistics.median(ts)
+        cpu = {"value": nnz / tmed / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"whole {args.workload} graph, sequential Hopcroft-Karp from the oracle's "
+                         f"{'empty' if empty else 'greedy'} start, median of {len(ts)} runs "
+                         f"({tmed * 1e3:.0f} ms each)"}
+
+    m.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": gteps, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
+                   "nnz": nnz, "n_rows": nr, "n_cols": nc,
+                   "variant": "APFB, GPUBFS-WR (one endpoint per root), persistent launch",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed before every step (256 MB write, outside the timed events)",
+                   "initial_matching": "none" if empty else
+                   f"GPU cheap matching, |M0|={greedy_card}, {greedy_ms:.3f} ms (untimed)"},
+        "max_matching": res.card,
+        "match_kernel_ms": match_ms,
+        "phases": st0["phases"], "levels": st0["levels"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_match (persistent, one launch per step)",
+                     "algorithmic_bytes": alg_bytes, "peak_kind": peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

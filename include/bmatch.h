@@ -1,0 +1,216 @@
+/*
+ * bmatch -- maximum cardinality matching in sparse bipartite graphs on one
+ * GB300 GPU (sm_103a), after Deveci, Kaya, Ucar and Catalyurek, "GPU accelerated
+ * maximum cardinality matching algorithms for bipartite graphs"
+ * (arXiv 1303.1379).
+ *
+ * The method (Section 3, Algorithm 1): starting from any matching, repeat
+ * phases until a phase finds no augmenting path.  A phase is a level-synchronous
+ * breadth-first search that starts from every unmatched column at once
+ * (GPUBFS, Algorithm 2, or GPUBFS-WR, Algorithm 4, which tracks the root of
+ * every search tree and stops a tree once a path for its root is found),
+ * then Alternate (Algorithm 3) flips the edges along the predecessor chains of
+ * the unmatched rows that the search reached, then FixMatching (Section 3)
+ * unmatches every row r with cmatch[rmatch[r]] != r.  APFB runs each search
+ * until no column is added; APsB stops it at the first level that reaches an
+ * unmatched row (Algorithm 1, the break inside the level loop).
+ *
+ * Conventions (Section 3): the graph is given by columns, CSR style:
+ * the rows adjacent to column c are row_idx[col_ptr[c] .. col_ptr[c+1]-1]
+ * (col_ptr has n_cols+1 entries, col_ptr[0] = 0, col_ptr[n_cols] = nnz, rows in
+ * [0, n_rows); rows inside a column need not be sorted; duplicates are
+ * tolerated).  A matching is rmatch[n_rows], cmatch[n_cols] with
+ * rmatch[r] = c and cmatch[c] = r for a matched pair and -1 for an unmatched
+ * vertex.  All indices are int32; nnz < 2^31.
+ *
+ * Execution: every call is issued on the stream given to bm_create and is
+ * synchronous with respect to the host unless stated otherwise (it returns
+ * after the work it enqueued has finished, so its status is final).  Device
+ * pointers are CUDA device (or managed) addresses on the current device.
+ *
+ * Errors: every entry point returns BM_OK (0), BM_INCOMPLETE (1, a caller-set
+ * phase limit was reached; the matching is valid but maybe not maximum) or a
+ * negative BM_ERR_* code.  The library never aborts, traps or hangs the GPU:
+ * every device-side wait is bounded by a time limit after which the kernel
+ * returns BM_ERR_TIMEOUT.  After an error the context's outputs are undefined
+ * and the error is sticky: later calls on that context return BM_ERR_STATE
+ * (destroy is always allowed).
+ */
+#ifndef BMATCH_H
+#define BMATCH_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BM_API __attribute__((visibility("default")))
+#else
+#define BM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BM_OK 0
+#define BM_INCOMPLETE 1
+#define BM_ERR_INVALID_ARG (-1)  /* null pointer, negative size, bad option   */
+#define BM_ERR_INVALID_CSR (-2)  /* col_ptr not monotone from 0 to nnz, or a row id outside [0, n_rows) */
+#define BM_ERR_NOMEM (-3)        /* device or pinned allocation failed         */
+#define BM_ERR_ITER_LIMIT (-4)   /* safety cap on phases or levels reached     */
+#define BM_ERR_TIMEOUT (-5)      /* a device-side barrier wait ran out of time */
+#define BM_ERR_CUDA (-6)         /* a CUDA runtime call failed                 */
+#define BM_ERR_STATE (-7)        /* earlier sticky error, or calls out of order */
+#define BM_ERR_UNSUPPORTED (-8)  /* device cannot run the cooperative launch   */
+#define BM_ERR_INVALID_MATCHING (-9) /* initial matching out of range or rmatch/cmatch not inverse */
+
+/* Algorithm 1: APFB keeps searching until no column is inserted; APsB stops
+ * at the first level that reaches an unmatched row. */
+#define BM_APFB 0
+#define BM_APSB 1
+/* Algorithm 2 (GPUBFS) or Algorithm 4 (GPUBFS-WR, root tracking + early exit). */
+#define BM_GPUBFS 0
+#define BM_GPUBFS_WR 1
+/* Device-resident loop over phases and levels (one cooperative launch per
+ * match) or the paper's host loop (one launch per level, host reads flags). */
+#define BM_DRIVER_PERSISTENT 0
+#define BM_DRIVER_HOST 1
+
+typedef struct bm_options {
+    int32_t mode;          /* BM_APFB (default) or BM_APSB                                  */
+    int32_t bfs;           /* BM_GPUBFS_WR (default) or BM_GPUBFS                           */
+    int32_t driver;        /* BM_DRIVER_PERSISTENT (default) or BM_DRIVER_HOST              */
+    int32_t wr_one_endpoint; /* GPUBFS-WR only: 1 (default) = a root accepts one endpoint,
+                                whose row is kept in the root's level slot as -(row), the
+                                refinement Section 3 describes for APsB-GPUBFS-WR; 0 = any
+                                number of endpoints per root, the root slot set to L0-2
+                                (Algorithm 4 as printed)                                   */
+    int32_t max_phases;    /* 0 = no limit besides the safety cap min(n_rows,n_cols)+2;
+                              > 0 = stop after that many phases with BM_INCOMPLETE          */
+    int32_t block_size;    /* threads per block, 0 = default (512); multiple of 32, <= 1024 */
+    int32_t blocks_per_sm; /* 0 = as many as fit (capped at 2 x 1024 threads per SM)        */
+    int32_t reserved0;
+    int64_t wait_timeout_ns;  /* limit of one device-side barrier wait; 0 = 5 s             */
+    int64_t total_timeout_ns; /* limit of one match launch; 0 = 120 s                       */
+    int64_t reserved[6];
+} bm_options;
+
+typedef struct bm_stats {
+    int32_t status;            /* same value the call returned                              */
+    int32_t phases;            /* outer iterations of Algorithm 1 (incl. the last, empty one) */
+    int32_t initial_card;      /* |M| of the installed matching                            */
+    int32_t final_card;        /* |M| returned                                              */
+    int64_t levels;            /* BFS levels over all phases (kernel calls in Fig. 2 terms) */
+    int64_t max_levels_in_phase;
+    int64_t columns_expanded;  /* frontier columns taken from the queues                    */
+    int64_t edges_scanned;     /* adjacency entries read by the BFS                         */
+    int64_t endpoints;         /* unmatched rows claimed by the BFS over all phases         */
+    int64_t fix_repairs;       /* rows and columns reset by FixMatching                      */
+    int64_t inserted;          /* columns the BFS added to a level                          */
+    int64_t edges_to_matched;  /* scanned edges whose row was matched                       */
+    int64_t alternate_steps;   /* columns rematched by Alternate                             */
+    int64_t kernel_ns;         /* device time of the persistent launch (0 for the host loop) */
+    int64_t reserved[2];
+} bm_stats;
+
+typedef struct bm_ctx bm_ctx;
+
+/* Fills *opt with the defaults listed above. */
+BM_API void bm_default_options(bm_options *opt);
+
+/* Library version as major*10000 + minor*100 + patch. */
+BM_API int32_t bm_version(void);
+
+/* Human readable name of a status code (static string, never NULL). */
+BM_API const char *bm_status_string(int32_t status);
+
+/*
+ * Creates a matching context for a graph with n_rows rows, n_cols columns and
+ * nnz edges (Section 3, "Data: cxadj, cadj, nc, nr").
+ *   col_ptr, row_idx: device arrays (n_cols+1 and nnz int32) borrowed by the
+ *     context until bm_destroy; the caller keeps ownership and must not free
+ *     or modify them meanwhile.  The CSR is validated on the device
+ *     (BM_ERR_INVALID_CSR).  Pass both NULL to let the context own device
+ *     storage of the given sizes, to be filled by bm_upload_csr or
+ *     bm_match_host.
+ *   stream: cudaStream_t to issue all work on (NULL = the legacy default stream).
+ *   opt: NULL for defaults.
+ * The context owns its workspace (matching, levels, roots, predecessors, one
+ * column queue, the endpoint list: about 4*(3*n_cols + 3*n_rows) bytes),
+ * allocated here.  The matching starts empty.
+ */
+BM_API int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *col_ptr,
+                  const int32_t *row_idx, void *stream, const bm_options *opt, bm_ctx **out);
+
+/* Copies a host CSR (n_cols+1 and nnz int32, pinned or pageable) into the
+ * context's own storage and validates it.  Only for contexts created with
+ * NULL col_ptr/row_idx (else BM_ERR_STATE). */
+BM_API int32_t bm_upload_csr(bm_ctx *ctx, const int32_t *h_col_ptr, const int32_t *h_row_idx);
+
+/* Replaces the options of an existing context (same meaning as in bm_create). */
+BM_API int32_t bm_set_options(bm_ctx *ctx, const bm_options *opt);
+
+/* Cheap initial matching on the GPU (the "cheap matching" initialisation of
+ * Section 4): every unmatched column scans its rows in order and claims the
+ * first unmatched one with an atomic compare-and-swap.  The result is a
+ * maximal matching added to the installed one; which maximal matching it is
+ * depends on thread timing.  *card_out (host, nullable) gets |M|. */
+BM_API int32_t bm_greedy(bm_ctx *ctx, int32_t *card_out);
+
+/* Installs an initial matching (Section 3: "any prior matching is given in
+ * rmatch and cmatch").  rmatch (n_rows) and cmatch (n_cols) are device arrays,
+ * copied; both NULL installs the empty matching.  Entries must be -1 or in
+ * range and the two arrays mutual inverses (else BM_ERR_INVALID_MATCHING);
+ * that every matched pair is an edge is the caller's promise, not checked. */
+BM_API int32_t bm_set_matching(bm_ctx *ctx, const int32_t *rmatch, const int32_t *cmatch);
+
+/* Copies the context's current matching to device arrays (either may be NULL). */
+BM_API int32_t bm_get_matching(bm_ctx *ctx, int32_t *rmatch_out, int32_t *cmatch_out);
+
+/*
+ * Algorithm 1 (APFB or APsB with GPUBFS or GPUBFS-WR, per the options) from
+ * the installed matching until no augmenting path remains, then copies the
+ * maximum matching to rmatch_out (n_rows) / cmatch_out (n_cols) (device,
+ * either may be NULL) and |M| to *card_out (host, nullable); *stats (host,
+ * nullable) gets counters.  The context keeps the result as its installed
+ * matching.
+ */
+BM_API int32_t bm_match(bm_ctx *ctx, int32_t *rmatch_out, int32_t *cmatch_out, int32_t *card_out,
+                 bm_stats *stats);
+
+/*
+ * One-shot call with HOST buffers: copies the CSR (h_col_ptr, h_row_idx) and
+ * the initial matching (h_rmatch, h_cmatch; both NULL = empty) to the device,
+ * runs bm_match, and writes the maximum matching back into h_rmatch/h_cmatch
+ * (if given) and |M| into *card_out.  The context must own its CSR storage
+ * (created with NULL col_ptr/row_idx).  Pinned host buffers make the copies
+ * asynchronous DMA; pageable ones work too.
+ */
+BM_API int32_t bm_match_host(bm_ctx *ctx, const int32_t *h_col_ptr, const int32_t *h_row_idx,
+                      int32_t *h_rmatch, int32_t *h_cmatch, int32_t *card_out,
+                      bm_stats *stats);
+
+/*
+ * One breadth-first search of Algorithm 1 (InitBfsArray, then the level loop
+ * with the context's BFS kind and mode) from the installed matching, without
+ * Alternate: for inspection and testing.  Outputs (device, each nullable):
+ *   level_out[n_cols]  bfs_array: L0 = 2 for unmatched columns, L0 + k for a
+ *                      column inserted at level k, L0 - 1 = 1 if never reached;
+ *                      under GPUBFS-WR a root whose path was found holds
+ *                      -(row) (one endpoint per root) or L0 - 2 = 0.
+ *   root_out[n_cols]   root column of each reached column (GPUBFS-WR), else -1.
+ *   pred_out[n_rows]   column from which each reached row was entered, or -1.
+ *   endpoints_out[..]  the unmatched rows the search claimed (capacity n_rows),
+ *   *n_endpoints_out   (host) their number.
+ * The installed matching is left unchanged.
+ */
+BM_API int32_t bm_bfs(bm_ctx *ctx, int32_t *level_out, int32_t *root_out, int32_t *pred_out,
+               int32_t *endpoints_out, int32_t *n_endpoints_out);
+
+/* Releases the context and its workspace (never the caller's buffers). */
+BM_API int32_t bm_destroy(bm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BMATCH_H */

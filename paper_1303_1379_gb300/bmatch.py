@@ -1,0 +1,262 @@
+"""Thin ctypes binding of the C-ABI declared in include/bmatch.h.
+
+Argument marshalling only: every step of the matching runs in libbmatch.so's
+CUDA kernels.  Device buffers are passed as torch CUDA tensors (int32,
+contiguous) or raw integer addresses; the stream defaults to torch's current
+stream.  If the library cannot be loaded, every call raises -- there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+from . import build as _build
+
+BM_OK = 0
+BM_INCOMPLETE = 1
+BM_ERR_INVALID_ARG = -1
+BM_ERR_INVALID_CSR = -2
+BM_ERR_NOMEM = -3
+BM_ERR_ITER_LIMIT = -4
+BM_ERR_TIMEOUT = -5
+BM_ERR_CUDA = -6
+BM_ERR_STATE = -7
+BM_ERR_UNSUPPORTED = -8
+BM_ERR_INVALID_MATCHING = -9
+
+BM_APFB, BM_APSB = 0, 1
+BM_GPUBFS, BM_GPUBFS_WR = 0, 1
+BM_DRIVER_PERSISTENT, BM_DRIVER_HOST = 0, 1
+
+EXPORTS = ("bm_default_options", "bm_version", "bm_status_string", "bm_create", "bm_upload_csr",
+           "bm_set_options", "bm_greedy", "bm_set_matching", "bm_get_matching", "bm_match",
+           "bm_match_host", "bm_bfs", "bm_destroy")
+
+
+class bm_options(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("bfs", ctypes.c_int32), ("driver", ctypes.c_int32),
+                ("wr_one_endpoint", ctypes.c_int32), ("max_phases", ctypes.c_int32),
+                ("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("wait_timeout_ns", ctypes.c_int64),
+                ("total_timeout_ns", ctypes.c_int64), ("reserved", ctypes.c_int64 * 6)]
+
+
+class bm_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("phases", ctypes.c_int32),
+                ("initial_card", ctypes.c_int32), ("final_card", ctypes.c_int32),
+                ("levels", ctypes.c_int64), ("max_levels_in_phase", ctypes.c_int64),
+                ("columns_expanded", ctypes.c_int64), ("edges_scanned", ctypes.c_int64),
+                ("endpoints", ctypes.c_int64), ("fix_repairs", ctypes.c_int64),
+                ("inserted", ctypes.c_int64), ("edges_to_matched", ctypes.c_int64),
+                ("alternate_steps", ctypes.c_int64), ("kernel_ns", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 2)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class BMError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+_lock = threading.Lock()
+_lib = None
+VP = ctypes.c_void_p
+I32P = ctypes.POINTER(ctypes.c_int32)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libbmatch.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing and _build.is_stale():
+                _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library missing: {path} (run __graft_entry__.build())")
+            lib = ctypes.CDLL(path)
+            lib.bm_default_options.argtypes = [ctypes.POINTER(bm_options)]
+            lib.bm_default_options.restype = None
+            lib.bm_version.argtypes = []
+            lib.bm_version.restype = ctypes.c_int32
+            lib.bm_status_string.argtypes = [ctypes.c_int32]
+            lib.bm_status_string.restype = ctypes.c_char_p
+            lib.bm_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, VP, VP, VP,
+                                      ctypes.POINTER(bm_options), ctypes.POINTER(VP)]
+            lib.bm_create.restype = ctypes.c_int32
+            lib.bm_upload_csr.argtypes = [VP, VP, VP]
+            lib.bm_upload_csr.restype = ctypes.c_int32
+            lib.bm_set_options.argtypes = [VP, ctypes.POINTER(bm_options)]
+            lib.bm_set_options.restype = ctypes.c_int32
+            lib.bm_greedy.argtypes = [VP, I32P]
+            lib.bm_greedy.restype = ctypes.c_int32
+            lib.bm_set_matching.argtypes = [VP, VP, VP]
+            lib.bm_set_matching.restype = ctypes.c_int32
+            lib.bm_get_matching.argtypes = [VP, VP, VP]
+            lib.bm_get_matching.restype = ctypes.c_int32
+            lib.bm_match.argtypes = [VP, VP, VP, I32P, ctypes.POINTER(bm_stats)]
+            lib.bm_match.restype = ctypes.c_int32
+            lib.bm_match_host.argtypes = [VP, VP, VP, VP, VP, I32P, ctypes.POINTER(bm_stats)]
+            lib.bm_match_host.restype = ctypes.c_int32
+            lib.bm_bfs.argtypes = [VP, VP, VP, VP, VP, I32P]
+            lib.bm_bfs.restype = ctypes.c_int32
+            lib.bm_destroy.argtypes = [VP]
+            lib.bm_destroy.restype = ctypes.c_int32
+            _lib = lib
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return load().bm_status_string(int(status)).decode()
+
+
+def _ptr(x) -> int | None:
+    """Device address of a torch tensor (int32, contiguous), an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError("expected a torch tensor, an address or None")
+    if x.dtype != torch.int32 or not x.is_contiguous():
+        raise TypeError("buffers must be contiguous int32 tensors")
+    return x.data_ptr()
+
+
+def _host_ptr(x) -> int | None:
+    if x is None:
+        return None
+    import numpy as np
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.int32 or not x.flags.c_contiguous:
+            raise TypeError("host buffers must be contiguous int32 arrays")
+        return x.ctypes.data
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.device.type != "cpu" or x.dtype != torch.int32 or not x.is_contiguous():
+            raise TypeError("host tensors must be contiguous int32 CPU tensors")
+        return x.data_ptr()
+    raise TypeError("expected a numpy array or a CPU tensor")
+
+
+def default_options(**kw) -> bm_options:
+    o = bm_options()
+    load().bm_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _current_stream() -> int:
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _check(rc: int, what: str, allow=(BM_OK,)) -> int:
+    if rc not in allow:
+        raise BMError(rc, what)
+    return rc
+
+
+@dataclass
+class MatchResult:
+    status: int
+    card: int
+    stats: dict
+
+
+class Matcher:
+    """One bm_ctx.  Either borrows device CSR tensors (col_ptr, row_idx) or,
+    when they are None, owns device storage for a CSR of the given sizes."""
+
+    def __init__(self, n_rows: int, n_cols: int, nnz: int, col_ptr=None, row_idx=None,
+                 stream: int | None = None, **options):
+        self._lib = load()
+        self.n_rows, self.n_cols, self.nnz = int(n_rows), int(n_cols), int(nnz)
+        self._keep = (col_ptr, row_idx)  # keep borrowed tensors alive
+        self.stream = _current_stream() if stream is None else stream
+        self.options = default_options(**options)
+        h = VP()
+        rc = self._lib.bm_create(self.n_rows, self.n_cols, self.nnz, _ptr(col_ptr), _ptr(row_idx),
+                                 self.stream, ctypes.byref(self.options), ctypes.byref(h))
+        _check(rc, "bm_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_options(self, **options):
+        o = default_options(**{**{k: getattr(self.options, k) for k, _ in bm_options._fields_
+                                  if k not in ("reserved",)}, **options})
+        _check(self._lib.bm_set_options(self._h, ctypes.byref(o)), "bm_set_options")
+        self.options = o
+
+    def upload_csr(self, h_col_ptr, h_row_idx):
+        _check(self._lib.bm_upload_csr(self._h, _host_ptr(h_col_ptr), _host_ptr(h_row_idx)),
+               "bm_upload_csr")
+
+    def greedy(self) -> int:
+        card = ctypes.c_int32(0)
+        _check(self._lib.bm_greedy(self._h, ctypes.byref(card)), "bm_greedy")
+        return card.value
+
+    def set_matching(self, rmatch=None, cmatch=None):
+        _check(self._lib.bm_set_matching(self._h, _ptr(rmatch), _ptr(cmatch)), "bm_set_matching")
+
+    def get_matching(self, rmatch_out=None, cmatch_out=None):
+        _check(self._lib.bm_get_matching(self._h, _ptr(rmatch_out), _ptr(cmatch_out)),
+               "bm_get_matching")
+
+    def match(self, rmatch_out=None, cmatch_out=None, allow_incomplete=False) -> MatchResult:
+        card = ctypes.c_int32(0)
+        st = bm_stats()
+        rc = self._lib.bm_match(self._h, _ptr(rmatch_out), _ptr(cmatch_out), ctypes.byref(card),
+                                ctypes.byref(st))
+        _check(rc, "bm_match", (BM_OK, BM_INCOMPLETE) if allow_incomplete else (BM_OK,))
+        return MatchResult(rc, card.value, st.as_dict())
+
+    def match_host(self, h_col_ptr, h_row_idx, h_rmatch=None, h_cmatch=None) -> MatchResult:
+        card = ctypes.c_int32(0)
+        st = bm_stats()
+        rc = self._lib.bm_match_host(self._h, _host_ptr(h_col_ptr), _host_ptr(h_row_idx),
+                                     _host_ptr(h_rmatch), _host_ptr(h_cmatch), ctypes.byref(card),
+                                     ctypes.byref(st))
+        _check(rc, "bm_match_host")
+        return MatchResult(rc, card.value, st.as_dict())
+
+    def bfs(self, level_out=None, root_out=None, pred_out=None, endpoints_out=None) -> int:
+        n = ctypes.c_int32(0)
+        _check(self._lib.bm_bfs(self._h, _ptr(level_out), _ptr(root_out), _ptr(pred_out),
+                                _ptr(endpoints_out), ctypes.byref(n)), "bm_bfs")
+        return n.value

@@ -1,0 +1,763 @@
+// bmatch: C-ABI of the GPU maximum cardinality bipartite matching path
+// (arXiv 1303.1379, Section 3, Algorithms 1-4), written for GB300 (sm_103a).
+//
+// Two drivers run the same device steps (bm_device.cuh):
+//  * persistent (default): ONE cooperative launch per bm_match runs every
+//    phase and every BFS level of Algorithm 1 on the device, separated by a
+//    software grid barrier whose waits are bounded by %globaltimer.  The host
+//    is not involved between levels (the paper reads the flags back after
+//    every level).
+//  * host: the paper's structure -- one launch per step, the host reads the
+//    level counters after each BFS level.  Kept for the variant comparison.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "bm_device.cuh"
+#include "bmatch.h"
+
+using bmd::Counters;
+using bmd::Ctl;
+using bmd::L0;
+using bmd::Params;
+
+namespace {
+
+constexpr int kVersion = 1 * 10000 + 0 * 100 + 0;
+constexpr int kDefaultBlock = 512;
+
+// ------------------------------------------------------------------ kernels
+
+// One launch per match: Algorithm 1 with both loops on the device.
+template <bool WR>
+__global__ void __launch_bounds__(1024, 1) k_match(Params p) {
+    using namespace bmd;
+    Ctl* ctl = p.ctl;
+    unsigned long long target = 0;
+    const unsigned long long t_start = globaltimer();
+    const unsigned long long deadline = t_start + (unsigned long long)p.total_ns;
+    const bool leader = (blockIdx.x == 0 && threadIdx.x == 0);
+    Counters cnt{0, 0, 0, 0, 0};
+    int step = 0;
+    int phases = 0;
+    int card = 0;
+    int status = 0;
+    long long levels_total = 0, levels_max = 0, eps_total = 0, ins_total = 0;
+    if (ld_volatile(&ctl->err) != 0) goto out;  // input validation failed before launch
+
+    for (;;) {
+        // ---- InitBfsArray (+ column half of FixMatching)
+        int s = step++;
+        if (leader) { ctl->qcnt[(s + 1) % 3] = 0; ctl->ecnt[(s + 1) % 3] = 0; }
+        step_init<WR>(p, s % 3, cnt);
+        if (!grid_sync(ctl, target, p.wait_ns, deadline)) goto out;
+        const int n_roots = ld_volatile(&ctl->qcnt[s % 3]);
+        card = p.nc - n_roots;
+        if (leader && phases == 0) ctl->initial_card = card;
+        if (n_roots == 0) break;  // every column matched
+        if (phases >= p.max_phases) {
+            status = p.phase_limit_is_error ? -4 /*BM_ERR_ITER_LIMIT*/ : 1 /*BM_INCOMPLETE*/;
+            break;
+        }
+        ++phases;
+
+        // ---- BFS, level by level (Algorithm 1 inner loop)
+        int qb = 0, qe = n_roots, lvl = L0, n_ep = 0, levels = 0;
+        for (;;) {
+            int s2 = step++;
+            if (leader) { ctl->qcnt[(s2 + 1) % 3] = 0; ctl->ecnt[(s2 + 1) % 3] = 0; }
+            step_expand<WR>(p, qb, qe, lvl, s2 % 3, n_ep, cnt);
+            if (!grid_sync(ctl, target, p.wait_ns, deadline)) goto out;
+            const int nq = ld_volatile(&ctl->qcnt[s2 % 3]);
+            n_ep += ld_volatile(&ctl->ecnt[s2 % 3]);
+            ++levels;
+            ins_total += nq;
+            if (nq == 0) break;                  // no vertex inserted
+            if (p.mode == 1 && n_ep > 0) break;  // APsB: stop at the first level with a path
+            qb = qe;
+            qe += nq;
+            ++lvl;
+        }
+        levels_total += levels;
+        if (levels > levels_max) levels_max = levels;
+        eps_total += n_ep;
+        if (leader) ctl->n_endpoints_last = n_ep;
+
+        if (p.bfs_only) {
+            step_release_endpoints(p, n_ep);
+            if (!grid_sync(ctl, target, p.wait_ns, deadline)) goto out;
+            break;
+        }
+        if (n_ep == 0) break;  // no augmenting path: the matching is maximum (Berge)
+
+        // ---- Alternate, then the row half of FixMatching
+        step_alternate(p, n_ep, levels + 2, cnt);
+        if (!grid_sync(ctl, target, p.wait_ns, deadline)) goto out;
+        step_fix_rows(p, cnt);
+        if (!grid_sync(ctl, target, p.wait_ns, deadline)) goto out;
+    }
+out:
+    flush_counters(p, cnt);
+    if (leader) {
+        int err = ld_volatile(&ctl->err);
+        ctl->status = err != 0 ? err : status;
+        ctl->card = card;
+        ctl->phases = phases + 1;  // counting the final search that found nothing
+        ctl->levels = levels_total;
+        ctl->max_levels = levels_max;
+        ctl->endpoints = eps_total;
+        ctl->inserted = ins_total;
+        ctl->kernel_ns = (long long)(globaltimer() - t_start);
+    }
+}
+
+// ---- per-step kernels of the host-driven loop (the paper's structure)
+template <bool WR>
+__global__ void __launch_bounds__(1024) k_init(Params p, int slot) {
+    Counters cnt{0, 0, 0, 0, 0};
+    bmd::step_init<WR>(p, slot, cnt);
+    bmd::flush_counters(p, cnt);
+}
+template <bool WR>
+__global__ void __launch_bounds__(1024) k_expand(Params p, int qb, int qe, int lvl, int slot, int ebase) {
+    Counters cnt{0, 0, 0, 0, 0};
+    bmd::step_expand<WR>(p, qb, qe, lvl, slot, ebase, cnt);
+    bmd::flush_counters(p, cnt);
+}
+__global__ void __launch_bounds__(1024) k_alternate(Params p, int n_ep, int cap) {
+    Counters cnt{0, 0, 0, 0, 0};
+    bmd::step_alternate(p, n_ep, cap, cnt);
+    bmd::flush_counters(p, cnt);
+}
+__global__ void __launch_bounds__(1024) k_fix(Params p) {
+    Counters cnt{0, 0, 0, 0, 0};
+    bmd::step_fix_rows(p, cnt);
+    bmd::flush_counters(p, cnt);
+}
+__global__ void __launch_bounds__(1024) k_release(Params p, int n_ep) {
+    bmd::step_release_endpoints(p, n_ep);
+}
+
+// ---- input checks, greedy, fills
+__global__ void k_check_csr(int nr, int nc, long long nnz, const int32_t* __restrict__ cp,
+                            const int32_t* __restrict__ ri, Ctl* ctl) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    bool bad = false;
+    if (tid == 0 && (cp[0] != 0 || (long long)cp[nc] != nnz)) bad = true;
+    for (long long c = tid; c < nc; c += nthr)
+        if (cp[c + 1] < cp[c]) bad = true;
+    for (long long e = tid; e < nnz; e += nthr) {
+        int r = __ldg(&ri[e]);
+        if (r < 0 || r >= nr) bad = true;
+    }
+    if (bad) bmd::set_error(ctl, BM_ERR_INVALID_CSR);
+}
+
+__global__ void k_check_matching(int nr, int nc, const int32_t* __restrict__ rm,
+                                 const int32_t* __restrict__ cm, Ctl* ctl) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthr = gridDim.x * blockDim.x;
+    bool bad = false;
+    for (int r = tid; r < nr; r += nthr) {
+        int c = rm[r];
+        if (c != -1 && (c < 0 || c >= nc || cm[c] != r)) bad = true;
+    }
+    for (int c = tid; c < nc; c += nthr) {
+        int r = cm[c];
+        if (r != -1 && (r < 0 || r >= nr || rm[r] != c)) bad = true;
+    }
+    if (bad) bmd::set_error(ctl, BM_ERR_INVALID_MATCHING);
+}
+
+__global__ void k_fill(int32_t* a, long long n, int v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+// Cheap matching: each unmatched column claims the first unmatched row of its
+// list by CAS.  A column stays unmatched only if all its rows were taken, so
+// the result is maximal.
+__global__ void k_greedy(int nc, const int32_t* __restrict__ cp, const int32_t* __restrict__ ri,
+                         int32_t* rm, int32_t* cm) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        if (cm[c] != -1) continue;
+        const int end = __ldg(&cp[c + 1]);
+        for (int e = __ldg(&cp[c]); e < end; ++e) {
+            const int r = __ldg(&ri[e]);
+            if (bmd::ld_volatile(&rm[r]) == -1 && atomicCAS(&rm[r], -1, c) == -1) {
+                cm[c] = r;
+                break;
+            }
+        }
+    }
+}
+
+__global__ void k_count_matched(int nc, const int32_t* __restrict__ cm, Ctl* ctl) {
+    int n = 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+        n += (cm[c] >= 0);
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) n += __shfl_down_sync(0xffffffffu, n, s);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(&ctl->card, n);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+struct bm_ctx {
+    int32_t nr = 0, nc = 0;
+    int64_t nnz = 0;
+    const int32_t* col_ptr = nullptr;
+    const int32_t* row_idx = nullptr;
+    bool owns_csr = false;
+    bool csr_ready = false;
+    cudaStream_t stream = nullptr;
+    bm_options opt{};
+    void* arena = nullptr;  // one device allocation for everything the context owns
+    int32_t* rmatch = nullptr;
+    int32_t* cmatch = nullptr;
+    int32_t* level = nullptr;
+    int32_t* root = nullptr;
+    int32_t* pred = nullptr;
+    int32_t* queue = nullptr;
+    int32_t* endpoints = nullptr;
+    Ctl* ctl = nullptr;
+    Ctl* h_ctl = nullptr;  // pinned mirror
+    int32_t sticky = 0;
+    int device = 0;
+    int num_sms = 0;
+    int coop_grid[2] = {0, 0};  // blocks of k_match<false>, k_match<true>
+    int block = kDefaultBlock;
+};
+
+namespace {
+
+int32_t cuda_fail(bm_ctx* ctx, cudaError_t e) {
+    if (e == cudaSuccess) return BM_OK;
+    (void)cudaGetLastError();
+    if (ctx) ctx->sticky = BM_ERR_CUDA;
+    return BM_ERR_CUDA;
+}
+
+#define BM_CUDA(ctx, call)                                  \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_); \
+    } while (0)
+
+int32_t check_options(const bm_options& o) {
+    if (o.mode != BM_APFB && o.mode != BM_APSB) return BM_ERR_INVALID_ARG;
+    if (o.bfs != BM_GPUBFS && o.bfs != BM_GPUBFS_WR) return BM_ERR_INVALID_ARG;
+    if (o.driver != BM_DRIVER_PERSISTENT && o.driver != BM_DRIVER_HOST) return BM_ERR_INVALID_ARG;
+    if (o.max_phases < 0 || o.blocks_per_sm < 0 || o.wait_timeout_ns < 0 || o.total_timeout_ns < 0)
+        return BM_ERR_INVALID_ARG;
+    if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 1024 || o.block_size % 32 != 0))
+        return BM_ERR_INVALID_ARG;
+    return BM_OK;
+}
+
+int grid_for(bm_ctx* ctx, int n) {  // plain launches: enough blocks to fill the GPU
+    long long want = ((long long)n + ctx->block - 1) / ctx->block;
+    long long cap = (long long)ctx->num_sms * (2048 / ctx->block);
+    if (want < 1) want = 1;
+    return (int)(want < cap ? want : cap);
+}
+
+int32_t configure(bm_ctx* ctx) {
+    ctx->block = ctx->opt.block_size ? ctx->opt.block_size : kDefaultBlock;
+    for (int wr = 0; wr < 2; ++wr) {
+        int per_sm = 0;
+        cudaError_t e = wr ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true>, ctx->block, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<false>, ctx->block, 0);
+        if (e != cudaSuccess) return cuda_fail(ctx, e);
+        int cap = 2048 / ctx->block;  // at most 2048 resident threads per SM
+        if (ctx->opt.blocks_per_sm > 0 && ctx->opt.blocks_per_sm < cap) cap = ctx->opt.blocks_per_sm;
+        if (per_sm > cap) per_sm = cap;
+        if (per_sm < 1) return BM_ERR_UNSUPPORTED;
+        ctx->coop_grid[wr] = per_sm * ctx->num_sms;
+    }
+    return BM_OK;
+}
+
+Params make_params(bm_ctx* ctx, bool bfs_only) {
+    Params p{};
+    p.nr = ctx->nr;
+    p.nc = ctx->nc;
+    p.col_ptr = ctx->col_ptr;
+    p.row_idx = ctx->row_idx;
+    p.rmatch = ctx->rmatch;
+    p.cmatch = ctx->cmatch;
+    p.level = ctx->level;
+    p.root = ctx->root;
+    p.pred = ctx->pred;
+    p.queue = ctx->queue;
+    p.endpoints = ctx->endpoints;
+    p.ctl = ctx->ctl;
+    p.mode = ctx->opt.mode;
+    p.one_ep = ctx->opt.wr_one_endpoint;
+    const int safety = (ctx->nr < ctx->nc ? ctx->nr : ctx->nc) + 2;
+    if (bfs_only) {
+        p.max_phases = 1;
+        p.phase_limit_is_error = 0;
+    } else if (ctx->opt.max_phases > 0 && ctx->opt.max_phases < safety) {
+        p.max_phases = ctx->opt.max_phases;
+        p.phase_limit_is_error = 0;
+    } else {
+        p.max_phases = safety;
+        p.phase_limit_is_error = 1;
+    }
+    p.bfs_only = bfs_only ? 1 : 0;
+    p.wait_ns = ctx->opt.wait_timeout_ns ? ctx->opt.wait_timeout_ns : 5000000000LL;
+    p.total_ns = ctx->opt.total_timeout_ns ? ctx->opt.total_timeout_ns : 120000000000LL;
+    return p;
+}
+
+int32_t validate_csr_async(bm_ctx* ctx) {
+    const long long work = ctx->nnz > ctx->nc ? ctx->nnz : (long long)ctx->nc + 1;
+    const int g = grid_for(ctx, (int)(work < (1 << 30) ? work : (1 << 30)));
+    k_check_csr<<<g, ctx->block, 0, ctx->stream>>>(ctx->nr, ctx->nc, ctx->nnz, ctx->col_ptr, ctx->row_idx, ctx->ctl);
+    BM_CUDA(ctx, cudaGetLastError());
+    return BM_OK;
+}
+
+int32_t sync_ctl(bm_ctx* ctx) {
+    BM_CUDA(ctx, cudaMemcpyAsync(ctx->h_ctl, ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    BM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return BM_OK;
+}
+
+// Host-driven Algorithm 1: one launch per step; the host reads the step
+// counters after every BFS level, as the paper's host loop reads its flags.
+template <bool WR>
+int32_t run_host_loop(bm_ctx* ctx, const Params& p) {
+    Ctl* h = ctx->h_ctl;
+    const int gb = grid_for(ctx, ctx->nc > ctx->nr ? ctx->nc : ctx->nr);
+    const int blk = ctx->block;
+    cudaStream_t st = ctx->stream;
+    int phases = 0, card = 0, status = 0;
+    long long levels_total = 0, levels_max = 0, eps_total = 0, ins_total = 0;
+    int step = 0;
+    auto clear_slot = [&](int slot) -> int32_t {
+        BM_CUDA(ctx, cudaMemsetAsync(&ctx->ctl->qcnt[slot], 0, sizeof(int32_t), st));
+        BM_CUDA(ctx, cudaMemsetAsync(&ctx->ctl->ecnt[slot], 0, sizeof(int32_t), st));
+        return BM_OK;
+    };
+    int32_t rc = sync_ctl(ctx);
+    if (rc) return rc;
+    if (h->err) return h->err;
+    for (;;) {
+        int s = step++;
+        if ((rc = clear_slot(s % 3))) return rc;
+        k_init<WR><<<gb, blk, 0, st>>>(p, s % 3);
+        BM_CUDA(ctx, cudaGetLastError());
+        if ((rc = sync_ctl(ctx))) return rc;
+        const int n_roots = h->qcnt[s % 3];
+        card = p.nc - n_roots;
+        if (phases == 0) {
+            BM_CUDA(ctx, cudaMemcpyAsync(&ctx->ctl->initial_card, &card, sizeof(int), cudaMemcpyHostToDevice, st));
+        }
+        if (n_roots == 0) break;
+        if (phases >= p.max_phases) { status = p.phase_limit_is_error ? BM_ERR_ITER_LIMIT : BM_INCOMPLETE; break; }
+        ++phases;
+        int qb = 0, qe = n_roots, lvl = L0, n_ep = 0, levels = 0;
+        for (;;) {
+            int s2 = step++;
+            if ((rc = clear_slot(s2 % 3))) return rc;
+            const int g = grid_for(ctx, qe - qb);
+            k_expand<WR><<<g, blk, 0, st>>>(p, qb, qe, lvl, s2 % 3, n_ep);
+            BM_CUDA(ctx, cudaGetLastError());
+            if ((rc = sync_ctl(ctx))) return rc;
+            const int nq = h->qcnt[s2 % 3];
+            n_ep += h->ecnt[s2 % 3];
+            ++levels;
+            ins_total += nq;
+            if (nq == 0) break;
+            if (p.mode == BM_APSB && n_ep > 0) break;
+            if (levels > p.nc + 2) return BM_ERR_ITER_LIMIT;
+            qb = qe;
+            qe += nq;
+            ++lvl;
+        }
+        levels_total += levels;
+        if (levels > levels_max) levels_max = levels;
+        eps_total += n_ep;
+        if (p.bfs_only) {
+            if (n_ep) k_release<<<grid_for(ctx, n_ep), blk, 0, st>>>(p, n_ep);
+            BM_CUDA(ctx, cudaGetLastError());
+            BM_CUDA(ctx, cudaMemcpyAsync(&ctx->ctl->n_endpoints_last, &n_ep, sizeof(int), cudaMemcpyHostToDevice, st));
+            break;
+        }
+        if (n_ep == 0) break;
+        k_alternate<<<grid_for(ctx, n_ep), blk, 0, st>>>(p, n_ep, levels + 2);
+        BM_CUDA(ctx, cudaGetLastError());
+        k_fix<<<grid_for(ctx, p.nr), blk, 0, st>>>(p);
+        BM_CUDA(ctx, cudaGetLastError());
+    }
+    if ((rc = sync_ctl(ctx))) return rc;
+    Ctl fin = *h;
+    fin.status = fin.err ? fin.err : status;
+    fin.card = card;
+    fin.phases = phases + 1;
+    fin.levels = levels_total;
+    fin.max_levels = levels_max;
+    fin.endpoints = eps_total;
+    fin.inserted = ins_total;
+    BM_CUDA(ctx, cudaMemcpyAsync(ctx->ctl, &fin, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    return sync_ctl(ctx);
+}
+
+// Runs the method (or one BFS) on the installed matching.  The control block
+// is cleared by the caller beforehand so that input checks queued before can
+// report through it.
+int32_t run(bm_ctx* ctx, bool bfs_only) {
+    Params p = make_params(ctx, bfs_only);
+    const bool wr = ctx->opt.bfs == BM_GPUBFS_WR;
+    if (ctx->opt.driver == BM_DRIVER_HOST) {
+        int32_t rc = wr ? run_host_loop<true>(ctx, p) : run_host_loop<false>(ctx, p);
+        if (rc < 0 && ctx->sticky == 0) ctx->sticky = rc;
+        return rc < 0 ? rc : ctx->h_ctl->status;
+    }
+    void* args[] = {&p};
+    cudaError_t e = wr ? cudaLaunchCooperativeKernel((const void*)k_match<true>, ctx->coop_grid[1], ctx->block, args, 0, ctx->stream)
+                       : cudaLaunchCooperativeKernel((const void*)k_match<false>, ctx->coop_grid[0], ctx->block, args, 0, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    return BM_OK;
+}
+
+int32_t finish(bm_ctx* ctx, int32_t* card_out, bm_stats* stats) {
+    int32_t rc = sync_ctl(ctx);
+    if (rc) return rc;
+    const Ctl& h = *ctx->h_ctl;
+    const int32_t status = h.status != 0 ? h.status : h.err;
+    if (status < 0) ctx->sticky = status;
+    if (card_out) *card_out = h.card;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->status = status;
+        stats->phases = h.phases;
+        stats->initial_card = h.initial_card;
+        stats->final_card = h.card;
+        stats->levels = h.levels;
+        stats->max_levels_in_phase = h.max_levels;
+        stats->columns_expanded = h.cols_expanded;
+        stats->edges_scanned = h.edges_scanned;
+        stats->endpoints = h.endpoints;
+        stats->fix_repairs = h.fix_repairs;
+        stats->inserted = h.inserted;
+        stats->edges_to_matched = h.edges_matched;
+        stats->alternate_steps = h.alt_steps;
+        stats->kernel_ns = h.kernel_ns;
+    }
+    return status;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C-ABI
+extern "C" {
+
+void bm_default_options(bm_options* opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->mode = BM_APFB;
+    opt->bfs = BM_GPUBFS_WR;
+    opt->driver = BM_DRIVER_PERSISTENT;
+    opt->wr_one_endpoint = 1;
+}
+
+int32_t bm_version(void) { return kVersion; }
+
+const char* bm_status_string(int32_t s) {
+    switch (s) {
+        case BM_OK: return "ok";
+        case BM_INCOMPLETE: return "phase limit reached (matching valid, maybe not maximum)";
+        case BM_ERR_INVALID_ARG: return "invalid argument";
+        case BM_ERR_INVALID_CSR: return "invalid CSR (col_ptr not monotone from 0 to nnz, or row id out of range)";
+        case BM_ERR_NOMEM: return "out of device or pinned memory";
+        case BM_ERR_ITER_LIMIT: return "safety cap on phases, levels or walk length reached";
+        case BM_ERR_TIMEOUT: return "device-side barrier wait timed out";
+        case BM_ERR_CUDA: return "CUDA runtime error";
+        case BM_ERR_STATE: return "context in error state or call out of order";
+        case BM_ERR_UNSUPPORTED: return "device cannot run the cooperative launch";
+        case BM_ERR_INVALID_MATCHING: return "initial matching out of range or rmatch/cmatch not inverse";
+        default: return "unknown status";
+    }
+}
+
+int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* col_ptr,
+                  const int32_t* row_idx, void* stream, const bm_options* opt, bm_ctx** out) {
+    if (!out) return BM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_rows < 0 || n_cols < 0 || nnz < 0 || nnz > 0x7fffffffLL) return BM_ERR_INVALID_ARG;
+    if (col_ptr == nullptr && row_idx != nullptr) return BM_ERR_INVALID_ARG;
+    if (col_ptr != nullptr && row_idx == nullptr && nnz > 0) return BM_ERR_INVALID_ARG;
+    bm_options o;
+    if (opt) o = *opt; else bm_default_options(&o);
+    int32_t rc = check_options(o);
+    if (rc) return rc;
+
+    bm_ctx* ctx = new (std::nothrow) bm_ctx();
+    if (!ctx) return BM_ERR_NOMEM;
+    ctx->nr = n_rows;
+    ctx->nc = n_cols;
+    ctx->nnz = nnz;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->opt = o;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete ctx;
+        return BM_ERR_CUDA;
+    }
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+    if (!coop) { delete ctx; return BM_ERR_UNSUPPORTED; }
+
+    // arena: [ctl][rmatch nr][cmatch nc][level nc][root nc][pred nr][queue nc][endpoints nr][csr?]
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t nr1 = (size_t)(n_rows ? n_rows : 1), nc1 = (size_t)(n_cols ? n_cols : 1);
+    size_t off_ctl = 0;
+    size_t off_rm = off_ctl + al(sizeof(Ctl));
+    size_t off_cm = off_rm + al(4 * nr1);
+    size_t off_lv = off_cm + al(4 * nc1);
+    size_t off_rt = off_lv + al(4 * nc1);
+    size_t off_pd = off_rt + al(4 * nc1);
+    size_t off_q = off_pd + al(4 * nr1);
+    size_t off_ep = off_q + al(4 * nc1);
+    size_t off_cp = off_ep + al(4 * nr1);
+    size_t total = off_cp;
+    const bool own = (col_ptr == nullptr);
+    size_t off_ri = 0;
+    if (own) {
+        off_ri = off_cp + al(4 * ((size_t)n_cols + 1));
+        total = off_ri + al(4 * (size_t)(nnz ? nnz : 1));
+    }
+    if (cudaMalloc(&ctx->arena, total) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete ctx;
+        return BM_ERR_NOMEM;
+    }
+    if (cudaMallocHost((void**)&ctx->h_ctl, sizeof(Ctl)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        cudaFree(ctx->arena);
+        delete ctx;
+        return BM_ERR_NOMEM;
+    }
+    char* a = (char*)ctx->arena;
+    ctx->ctl = (Ctl*)(a + off_ctl);
+    ctx->rmatch = (int32_t*)(a + off_rm);
+    ctx->cmatch = (int32_t*)(a + off_cm);
+    ctx->level = (int32_t*)(a + off_lv);
+    ctx->root = (int32_t*)(a + off_rt);
+    ctx->pred = (int32_t*)(a + off_pd);
+    ctx->queue = (int32_t*)(a + off_q);
+    ctx->endpoints = (int32_t*)(a + off_ep);
+    if (own) {
+        ctx->owns_csr = true;
+        ctx->col_ptr = (int32_t*)(a + off_cp);
+        ctx->row_idx = (int32_t*)(a + off_ri);
+    } else {
+        ctx->col_ptr = col_ptr;
+        ctx->row_idx = row_idx;
+    }
+    rc = configure(ctx);
+    if (rc) { bm_destroy(ctx); return rc; }
+    cudaStream_t st = ctx->stream;
+    if (cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->rmatch, 0xff, 4 * nr1, st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->cmatch, 0xff, 4 * nc1, st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->pred, 0xff, 4 * nr1, st) != cudaSuccess) {
+        cuda_fail(ctx, cudaGetLastError());
+        bm_destroy(ctx);
+        return BM_ERR_CUDA;
+    }
+    if (!own) {
+        rc = validate_csr_async(ctx);
+        if (!rc) rc = sync_ctl(ctx);
+        if (!rc && ctx->h_ctl->err) rc = ctx->h_ctl->err;
+        if (rc) { bm_destroy(ctx); return rc; }
+        ctx->csr_ready = true;
+    } else {
+        rc = sync_ctl(ctx);
+        if (rc) { bm_destroy(ctx); return rc; }
+    }
+    *out = ctx;
+    return BM_OK;
+}
+
+int32_t bm_set_options(bm_ctx* ctx, const bm_options* opt) {
+    if (!ctx || !opt) return BM_ERR_INVALID_ARG;
+    if (ctx->sticky) return BM_ERR_STATE;
+    int32_t rc = check_options(*opt);
+    if (rc) return rc;
+    ctx->opt = *opt;
+    return configure(ctx);
+}
+
+int32_t bm_upload_csr(bm_ctx* ctx, const int32_t* h_col_ptr, const int32_t* h_row_idx) {
+    if (!ctx || !h_col_ptr || (!h_row_idx && ctx->nnz > 0)) return BM_ERR_INVALID_ARG;
+    if (ctx->sticky || !ctx->owns_csr) return BM_ERR_STATE;
+    cudaStream_t st = ctx->stream;
+    BM_CUDA(ctx, cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), st));
+    BM_CUDA(ctx, cudaMemcpyAsync((void*)ctx->col_ptr, h_col_ptr, 4 * ((size_t)ctx->nc + 1), cudaMemcpyHostToDevice, st));
+    if (ctx->nnz)
+        BM_CUDA(ctx, cudaMemcpyAsync((void*)ctx->row_idx, h_row_idx, 4 * (size_t)ctx->nnz, cudaMemcpyHostToDevice, st));
+    int32_t rc = validate_csr_async(ctx);
+    if (!rc) rc = sync_ctl(ctx);
+    if (rc) return rc;
+    if (ctx->h_ctl->err) { ctx->csr_ready = false; return ctx->h_ctl->err; }
+    ctx->csr_ready = true;
+    return BM_OK;
+}
+
+int32_t bm_greedy(bm_ctx* ctx, int32_t* card_out) {
+    if (!ctx) return BM_ERR_INVALID_ARG;
+    if (ctx->sticky || !ctx->csr_ready) return BM_ERR_STATE;
+    cudaStream_t st = ctx->stream;
+    BM_CUDA(ctx, cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), st));
+    if (ctx->nc) {
+        k_greedy<<<grid_for(ctx, ctx->nc), ctx->block, 0, st>>>(ctx->nc, ctx->col_ptr, ctx->row_idx, ctx->rmatch, ctx->cmatch);
+        BM_CUDA(ctx, cudaGetLastError());
+        k_count_matched<<<grid_for(ctx, ctx->nc), ctx->block, 0, st>>>(ctx->nc, ctx->cmatch, ctx->ctl);
+        BM_CUDA(ctx, cudaGetLastError());
+    }
+    int32_t rc = sync_ctl(ctx);
+    if (rc) return rc;
+    if (card_out) *card_out = ctx->h_ctl->card;
+    return BM_OK;
+}
+
+int32_t bm_set_matching(bm_ctx* ctx, const int32_t* rmatch, const int32_t* cmatch) {
+    if (!ctx || ((rmatch == nullptr) != (cmatch == nullptr))) return BM_ERR_INVALID_ARG;
+    if (ctx->sticky) return BM_ERR_STATE;
+    cudaStream_t st = ctx->stream;
+    if (!rmatch) {
+        BM_CUDA(ctx, cudaMemsetAsync(ctx->rmatch, 0xff, 4 * (size_t)ctx->nr, st));
+        BM_CUDA(ctx, cudaMemsetAsync(ctx->cmatch, 0xff, 4 * (size_t)ctx->nc, st));
+        return BM_OK;
+    }
+    BM_CUDA(ctx, cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), st));
+    if (ctx->nr) BM_CUDA(ctx, cudaMemcpyAsync(ctx->rmatch, rmatch, 4 * (size_t)ctx->nr, cudaMemcpyDeviceToDevice, st));
+    if (ctx->nc) BM_CUDA(ctx, cudaMemcpyAsync(ctx->cmatch, cmatch, 4 * (size_t)ctx->nc, cudaMemcpyDeviceToDevice, st));
+    k_check_matching<<<grid_for(ctx, ctx->nr > ctx->nc ? ctx->nr : ctx->nc), ctx->block, 0, st>>>(ctx->nr, ctx->nc, ctx->rmatch, ctx->cmatch, ctx->ctl);
+    BM_CUDA(ctx, cudaGetLastError());
+    int32_t rc = sync_ctl(ctx);
+    if (rc) return rc;
+    if (ctx->h_ctl->err) {
+        // leave a valid (empty) matching installed
+        cudaMemsetAsync(ctx->rmatch, 0xff, 4 * (size_t)ctx->nr, st);
+        cudaMemsetAsync(ctx->cmatch, 0xff, 4 * (size_t)ctx->nc, st);
+        cudaStreamSynchronize(st);
+        return ctx->h_ctl->err;
+    }
+    return BM_OK;
+}
+
+int32_t bm_get_matching(bm_ctx* ctx, int32_t* rmatch_out, int32_t* cmatch_out) {
+    if (!ctx) return BM_ERR_INVALID_ARG;
+    if (ctx->sticky) return BM_ERR_STATE;
+    cudaStream_t st = ctx->stream;
+    if (rmatch_out && ctx->nr) BM_CUDA(ctx, cudaMemcpyAsync(rmatch_out, ctx->rmatch, 4 * (size_t)ctx->nr, cudaMemcpyDeviceToDevice, st));
+    if (cmatch_out && ctx->nc) BM_CUDA(ctx, cudaMemcpyAsync(cmatch_out, ctx->cmatch, 4 * (size_t)ctx->nc, cudaMemcpyDeviceToDevice, st));
+    BM_CUDA(ctx, cudaStreamSynchronize(st));
+    return BM_OK;
+}
+
+int32_t bm_match(bm_ctx* ctx, int32_t* rmatch_out, int32_t* cmatch_out, int32_t* card_out, bm_stats* stats) {
+    if (!ctx) return BM_ERR_INVALID_ARG;
+    if (ctx->sticky || !ctx->csr_ready) return BM_ERR_STATE;
+    cudaStream_t st = ctx->stream;
+    BM_CUDA(ctx, cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), st));
+    int32_t rc = run(ctx, false);
+    if (rc < 0) return rc;
+    if (rmatch_out && ctx->nr) BM_CUDA(ctx, cudaMemcpyAsync(rmatch_out, ctx->rmatch, 4 * (size_t)ctx->nr, cudaMemcpyDeviceToDevice, st));
+    if (cmatch_out && ctx->nc) BM_CUDA(ctx, cudaMemcpyAsync(cmatch_out, ctx->cmatch, 4 * (size_t)ctx->nc, cudaMemcpyDeviceToDevice, st));
+    return finish(ctx, card_out, stats);
+}
+
+int32_t bm_match_host(bm_ctx* ctx, const int32_t* h_col_ptr, const int32_t* h_row_idx,
+                      int32_t* h_rmatch, int32_t* h_cmatch, int32_t* card_out, bm_stats* stats) {
+    if (!ctx || !h_col_ptr || (!h_row_idx && ctx->nnz > 0) || ((h_rmatch == nullptr) != (h_cmatch == nullptr)))
+        return BM_ERR_INVALID_ARG;
+    if (ctx->sticky || !ctx->owns_csr) return BM_ERR_STATE;
+    cudaStream_t st = ctx->stream;
+    BM_CUDA(ctx, cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), st));
+    BM_CUDA(ctx, cudaMemcpyAsync((void*)ctx->col_ptr, h_col_ptr, 4 * ((size_t)ctx->nc + 1), cudaMemcpyHostToDevice, st));
+    if (ctx->nnz)
+        BM_CUDA(ctx, cudaMemcpyAsync((void*)ctx->row_idx, h_row_idx, 4 * (size_t)ctx->nnz, cudaMemcpyHostToDevice, st));
+    if (h_rmatch) {
+        if (ctx->nr) BM_CUDA(ctx, cudaMemcpyAsync(ctx->rmatch, h_rmatch, 4 * (size_t)ctx->nr, cudaMemcpyHostToDevice, st));
+        if (ctx->nc) BM_CUDA(ctx, cudaMemcpyAsync(ctx->cmatch, h_cmatch, 4 * (size_t)ctx->nc, cudaMemcpyHostToDevice, st));
+    } else {
+        BM_CUDA(ctx, cudaMemsetAsync(ctx->rmatch, 0xff, 4 * (size_t)ctx->nr, st));
+        BM_CUDA(ctx, cudaMemsetAsync(ctx->cmatch, 0xff, 4 * (size_t)ctx->nc, st));
+    }
+    // input checks report through the control block; the match launch then
+    // returns at once if one failed
+    int32_t rc = validate_csr_async(ctx);
+    if (rc) return rc;
+    k_check_matching<<<grid_for(ctx, ctx->nr > ctx->nc ? ctx->nr : ctx->nc), ctx->block, 0, st>>>(ctx->nr, ctx->nc, ctx->rmatch, ctx->cmatch, ctx->ctl);
+    BM_CUDA(ctx, cudaGetLastError());
+    ctx->csr_ready = true;
+    if (ctx->opt.driver == BM_DRIVER_HOST) {
+        rc = sync_ctl(ctx);
+        if (rc) return rc;
+        if (ctx->h_ctl->err) { ctx->csr_ready = false; return ctx->h_ctl->err; }
+    }
+    rc = run(ctx, false);
+    if (rc < 0) return rc;
+    if (h_rmatch) {
+        if (ctx->nr) BM_CUDA(ctx, cudaMemcpyAsync(h_rmatch, ctx->rmatch, 4 * (size_t)ctx->nr, cudaMemcpyDeviceToHost, st));
+        if (ctx->nc) BM_CUDA(ctx, cudaMemcpyAsync(h_cmatch, ctx->cmatch, 4 * (size_t)ctx->nc, cudaMemcpyDeviceToHost, st));
+    }
+    rc = finish(ctx, card_out, stats);
+    if (rc == BM_ERR_INVALID_CSR || rc == BM_ERR_INVALID_MATCHING) {
+        ctx->csr_ready = false;
+        ctx->sticky = 0;  // bad input is not a broken context
+        cudaMemsetAsync(ctx->rmatch, 0xff, 4 * (size_t)ctx->nr, st);
+        cudaMemsetAsync(ctx->cmatch, 0xff, 4 * (size_t)ctx->nc, st);
+        cudaStreamSynchronize(st);
+    }
+    return rc;
+}
+
+int32_t bm_bfs(bm_ctx* ctx, int32_t* level_out, int32_t* root_out, int32_t* pred_out,
+               int32_t* endpoints_out, int32_t* n_endpoints_out) {
+    if (!ctx) return BM_ERR_INVALID_ARG;
+    if (ctx->sticky || !ctx->csr_ready) return BM_ERR_STATE;
+    cudaStream_t st = ctx->stream;
+    BM_CUDA(ctx, cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), st));
+    BM_CUDA(ctx, cudaMemsetAsync(ctx->pred, 0xff, 4 * (size_t)(ctx->nr ? ctx->nr : 1), st));
+    if (ctx->opt.bfs != BM_GPUBFS_WR && ctx->nc) {
+        k_fill<<<grid_for(ctx, ctx->nc), ctx->block, 0, st>>>(ctx->root, ctx->nc, -1);
+        BM_CUDA(ctx, cudaGetLastError());
+    }
+    int32_t rc = run(ctx, true);
+    if (rc < 0) return rc;
+    rc = sync_ctl(ctx);
+    if (rc) return rc;
+    const int n_ep = ctx->h_ctl->n_endpoints_last;
+    if (level_out && ctx->nc) BM_CUDA(ctx, cudaMemcpyAsync(level_out, ctx->level, 4 * (size_t)ctx->nc, cudaMemcpyDeviceToDevice, st));
+    if (root_out && ctx->nc) BM_CUDA(ctx, cudaMemcpyAsync(root_out, ctx->root, 4 * (size_t)ctx->nc, cudaMemcpyDeviceToDevice, st));
+    if (pred_out && ctx->nr) BM_CUDA(ctx, cudaMemcpyAsync(pred_out, ctx->pred, 4 * (size_t)ctx->nr, cudaMemcpyDeviceToDevice, st));
+    if (endpoints_out && n_ep) BM_CUDA(ctx, cudaMemcpyAsync(endpoints_out, ctx->endpoints, 4 * (size_t)n_ep, cudaMemcpyDeviceToDevice, st));
+    if (n_endpoints_out) *n_endpoints_out = n_ep;
+    rc = finish(ctx, nullptr, nullptr);
+    return rc == BM_INCOMPLETE ? BM_OK : rc;
+}
+
+int32_t bm_destroy(bm_ctx* ctx) {
+    if (!ctx) return BM_ERR_INVALID_ARG;
+    if (ctx->stream || ctx->arena) cudaStreamSynchronize(ctx->stream);
+    if (ctx->arena) cudaFree(ctx->arena);
+    if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
+    (void)cudaGetLastError();
+    delete ctx;
+    return BM_OK;
+}
+
+}  // extern "C"
