@@ -62,6 +62,7 @@ extern "C" {
 #define BM_ERR_STATE (-7)        /* earlier sticky error, or calls out of order */
 #define BM_ERR_UNSUPPORTED (-8)  /* device cannot run the cooperative launch   */
 #define BM_ERR_INVALID_MATCHING (-9) /* initial matching out of range or rmatch/cmatch not inverse */
+#define BM_ERR_TOO_LARGE (-10)   /* graph too large for bm_match_noalloc's fixed scratch */
 
 /* Algorithm 1: APFB keeps searching until no column is inserted; APsB stops
  * at the first level that reaches an unmatched row. */
@@ -208,6 +209,44 @@ BM_API int32_t bm_bfs(bm_ctx *ctx, int32_t *level_out, int32_t *root_out, int32_
 
 /* Releases the context and its workspace (never the caller's buffers). */
 BM_API int32_t bm_destroy(bm_ctx *ctx);
+
+/*
+ * Allocation-free matching (no counterpart in the paper; an addition for
+ * callers that may not allocate).
+ *
+ * Some callers cannot call cudaMalloc: code running inside a memory pool or
+ * arena that owns all device memory of the process, plugins whose host
+ * application forbids allocation after start-up, and real-time loops where an
+ * allocation could block or fail mid-run.  This entry point runs the same
+ * persistent matching kernel as bm_match (APFB, GPUBFS-WR, one endpoint per
+ * root) with no context and no allocation: its working arrays live in one
+ * file-scope device array of BM_NOALLOC_SCRATCH_BYTES, which every GPU that
+ * loads this library holds until the process exits.
+ *
+ *   col_ptr, row_idx  device CSR of the columns, as for bm_create (read only).
+ *   rmatch, cmatch    device arrays (n_rows, n_cols): the initial matching on
+ *                     entry (-1 everywhere for none), the maximum matching on
+ *                     return.  Caller-owned.
+ *   stream            cudaStream_t for all work (NULL = legacy default stream).
+ *   card_out          host, nullable: |M|.
+ * Size limit: 512 + 4*(3*n_cols + 2*n_rows) bytes (each array rounded up to
+ * 256 bytes) must fit in BM_NOALLOC_SCRATCH_BYTES, else BM_ERR_TOO_LARGE is
+ * returned before any GPU work.  Invalid CSR or matching: BM_ERR_INVALID_CSR /
+ * BM_ERR_INVALID_MATCHING (rmatch/cmatch unchanged then).
+ * The first call on a device finds the scratch array's device address
+ * (cudaGetSymbolAddress) and the launch size; make that first call before any
+ * stream capture.  Calls never allocate (no cudaMalloc, cudaFree or library
+ * routine that allocates) and return after the work finished.  All calls share
+ * the one scratch array, which keeps the previous call's contents (the parts
+ * that must start at zero are cleared by each call): calls that overlap on the
+ * GPU -- concurrent calls on different streams or host threads -- race and
+ * must be serialised by the caller.
+ */
+#define BM_NOALLOC_SCRATCH_BYTES (32u << 20)
+BM_API int32_t bm_match_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
+                                const int32_t *col_ptr, const int32_t *row_idx,
+                                int32_t *rmatch, int32_t *cmatch, void *stream,
+                                int32_t *card_out);
 
 #ifdef __cplusplus
 }

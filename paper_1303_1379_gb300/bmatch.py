@@ -26,6 +26,7 @@ BM_ERR_CUDA = -6
 BM_ERR_STATE = -7
 BM_ERR_UNSUPPORTED = -8
 BM_ERR_INVALID_MATCHING = -9
+BM_ERR_TOO_LARGE = -10
 
 BM_APFB, BM_APSB = 0, 1
 BM_GPUBFS, BM_GPUBFS_WR = 0, 1
@@ -260,3 +261,21 @@ class Matcher:
         _check(self._lib.bm_bfs(self._h, _ptr(level_out), _ptr(root_out), _ptr(pred_out),
                                 _ptr(endpoints_out), ctypes.byref(n)), "bm_bfs")
         return n.value
+
+
+def bm_match_noalloc(n_rows: int, n_cols: int, nnz: int, col_ptr, row_idx, rmatch, cmatch,
+                     stream: int | None = None):
+    """Allocation-free matching through the C-ABI (see bm_match_noalloc in
+    bmatch.h): for callers that cannot allocate device memory.  rmatch/cmatch
+    (device int32) hold the initial matching and receive the maximum one.
+    Returns (status, |M|); the status is not raised so callers can see
+    BM_ERR_TOO_LARGE and friends."""
+    lib = load()
+    fn = lib.bm_match_noalloc
+    fn.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, VP, VP, VP, VP, VP, I32P]
+    fn.restype = ctypes.c_int32
+    card = ctypes.c_int32(0)
+    st = _current_stream() if stream is None else stream
+    rc = fn(int(n_rows), int(n_cols), int(nnz), _ptr(col_ptr), _ptr(row_idx), _ptr(rmatch),
+            _ptr(cmatch), st, ctypes.byref(card))
+    return int(rc), card.value

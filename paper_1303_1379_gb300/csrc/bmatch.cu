@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "bm_device.cuh"
 #include "bmatch.h"
@@ -484,6 +485,7 @@ const char* bm_status_string(int32_t s) {
         case BM_ERR_STATE: return "context in error state or call out of order";
         case BM_ERR_UNSUPPORTED: return "device cannot run the cooperative launch";
         case BM_ERR_INVALID_MATCHING: return "initial matching out of range or rmatch/cmatch not inverse";
+        case BM_ERR_TOO_LARGE: return "graph too large for the allocation-free entry point's scratch";
         default: return "unknown status";
     }
 }
@@ -761,3 +763,133 @@ int32_t bm_destroy(bm_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free entry point
+// For callers that may not allocate device memory (see bm_match_noalloc in
+// bmatch.h): the working arrays of the matching kernel live in this fixed
+// file-scope array instead of a context's allocation.
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[BM_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+
+struct NoallocDevice {
+    bool ready;
+    unsigned char* scratch;  // device address of g_noalloc_scratch on this device
+    int grid;                // cooperative grid of k_match<true>
+    int block;
+    int sms;
+};
+NoallocDevice g_noalloc_dev[kMaxDevices];
+std::mutex g_noalloc_mutex;
+
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Once per device, with that device current: the host-side name of the array
+// is not a device address, so look the address up and keep it.
+int32_t noalloc_setup(int dev, NoallocDevice* out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoallocDevice& d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || ptr == nullptr) { (void)cudaGetLastError(); return BM_ERR_CUDA; }
+        int sms = 0, coop = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true>, kDefaultBlock, 0) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return BM_ERR_CUDA;
+        }
+        if (!coop || per_sm < 1) return BM_ERR_UNSUPPORTED;
+        if (per_sm > 2048 / kDefaultBlock) per_sm = 2048 / kDefaultBlock;
+        d.scratch = (unsigned char*)ptr;
+        d.grid = per_sm * sms;
+        d.block = kDefaultBlock;
+        d.sms = sms;
+        d.ready = true;
+    }
+    *out = d;
+    return BM_OK;
+}
+
+}  // namespace
+
+extern "C" int32_t bm_match_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
+                                    const int32_t* col_ptr, const int32_t* row_idx,
+                                    int32_t* rmatch, int32_t* cmatch, void* stream,
+                                    int32_t* card_out) {
+    if (n_rows < 0 || n_cols < 0 || nnz < 0 || nnz > 0x7fffffffLL) return BM_ERR_INVALID_ARG;
+    if (!col_ptr || (!row_idx && nnz > 0) || (!rmatch && n_rows > 0) || (!cmatch && n_cols > 0))
+        return BM_ERR_INVALID_ARG;
+    const size_t nr = (size_t)n_rows, nc = (size_t)n_cols;
+    const size_t off_lv = round256(sizeof(Ctl));
+    const size_t off_rt = off_lv + round256(4 * nc);
+    const size_t off_pd = off_rt + round256(4 * nc);
+    const size_t off_q = off_pd + round256(4 * nr);
+    const size_t off_ep = off_q + round256(4 * nc);
+    const size_t need = off_ep + round256(4 * nr);
+    if (need > (size_t)BM_NOALLOC_SCRATCH_BYTES) return BM_ERR_TOO_LARGE;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { (void)cudaGetLastError(); return BM_ERR_CUDA; }
+    if (dev < 0 || dev >= kMaxDevices) return BM_ERR_UNSUPPORTED;
+    NoallocDevice d;
+    int32_t rc = noalloc_setup(dev, &d);
+    if (rc) return rc;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* s = d.scratch;
+    Ctl* ctl = (Ctl*)s;
+    Params p{};
+    p.nr = n_rows;
+    p.nc = n_cols;
+    p.col_ptr = col_ptr;
+    p.row_idx = row_idx;
+    p.rmatch = rmatch;
+    p.cmatch = cmatch;
+    p.level = (int32_t*)(s + off_lv);
+    p.root = (int32_t*)(s + off_rt);
+    p.pred = (int32_t*)(s + off_pd);
+    p.queue = (int32_t*)(s + off_q);
+    p.endpoints = (int32_t*)(s + off_ep);
+    p.ctl = ctl;
+    p.mode = BM_APFB;
+    p.one_ep = 1;
+    p.max_phases = (n_rows < n_cols ? n_rows : n_cols) + 2;
+    p.phase_limit_is_error = 1;
+    p.bfs_only = 0;
+    p.wait_ns = 5000000000LL;
+    p.total_ns = 120000000000LL;
+
+    // the control block (barrier counter, step counters, error word) must start at zero;
+    // the other arrays are written before they are read
+    if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), st) != cudaSuccess) { (void)cudaGetLastError(); return BM_ERR_CUDA; }
+    const int threads = 2048 / d.block * d.sms;
+    const long long work = nnz > n_cols ? nnz : (long long)n_cols + 1;
+    int g = (int)((work + d.block - 1) / d.block);
+    if (g > threads) g = threads;
+    if (g < 1) g = 1;
+    k_check_csr<<<g, d.block, 0, st>>>(n_rows, n_cols, nnz, col_ptr, row_idx, ctl);
+    const int n_max = n_rows > n_cols ? n_rows : n_cols;
+    int g2 = (n_max + d.block - 1) / d.block;
+    if (g2 > threads) g2 = threads;
+    if (g2 < 1) g2 = 1;
+    k_check_matching<<<g2, d.block, 0, st>>>(n_rows, n_cols, rmatch, cmatch, ctl);
+    if (cudaGetLastError() != cudaSuccess) return BM_ERR_CUDA;
+    void* args[] = {&p};
+    if (cudaLaunchCooperativeKernel((const void*)k_match<true>, d.grid, d.block, args, 0, st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return BM_ERR_CUDA;
+    }
+    Ctl h;  // pageable host copy of the control block
+    if (cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return BM_ERR_CUDA;
+    }
+    const int32_t status = h.status != 0 ? h.status : h.err;
+    if (card_out) *card_out = h.card;
+    return status;
+}
