@@ -3,7 +3,7 @@
 // One phase of Algorithm 1 of arXiv 1303.1379 (Section 3) is
 //   InitBfsArray -> BFS levels (Algorithm 2 GPUBFS / Algorithm 4 GPUBFS-WR)
 //   -> Alternate (Algorithm 3) -> FixMatching.
-// This header holds those steps as device functions over "all threads of the
+// This header holds those steps as device functions over "all blocks of the
 // grid", so that the persistent kernel (one launch per match, grid barriers
 // between steps) and the per-step kernels of the host-driven loop run the
 // same code.
@@ -14,17 +14,21 @@
 //    appended to one per-phase queue; a level expands only its own queue
 //    segment, so a level costs O(frontier + its edges), not O(nc).
 //  * Insertions are claimed with a test-then-CAS on the column's level entry;
-//    the single winner writes pred/root and appends the column (warp-
-//    aggregated atomics).  The paper's atomic-free writes let several threads
-//    insert the same column; a queue needs exactly one.
+//    the single winner writes pred/root and appends the column.  The paper's
+//    atomic-free writes let several threads insert the same column; a queue
+//    needs exactly one.
 //  * Free rows are claimed with a CAS -1 -> -2 on rmatch (the paper's plain
 //    store of -2), so every endpoint has exactly one predecessor and is
 //    appended once to an endpoint list; Alternate walks that list instead of
 //    scanning all rows for -2.
-//  * A warp expands 32 queue entries at a time: columns with more than 32
-//    rows are scanned by the whole warp, one after another; the rest are
-//    expanded by a warp-wide prefix sum over their degrees, so every lane
-//    handles one edge per iteration whatever the degree mix.
+//  * Load balance: a block takes a tile of queue entries (tiles are handed out
+//    by an atomic counter), computes a block-wide prefix sum of their degrees
+//    and then every thread handles edges tid, tid + blockDim, ... of the
+//    tile's concatenated adjacency, ILP edges at a time (independent loads in
+//    flight), finding each edge's column by binary search in shared memory.
+//    A column of degree 60,000 and a column of degree 1 cost the same per edge.
+//  * Appends go to a per-block shared-memory buffer that is flushed with one
+//    global atomic per tile.
 #pragma once
 #include <cooperative_groups.h>
 #include <cstdint>
@@ -35,23 +39,29 @@ namespace cg = cooperative_groups;
 
 constexpr int L0 = 2;  // BFS start level (Section 3 chooses L0 = 2)
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int MAX_BLOCK = 1024;
+constexpr int QBUF = 4096;  // per-block append buffer (entries)
+constexpr int ILP = 4;      // edges per thread in flight
 
 // Control block in device memory, cleared before every launch.  Per-step
 // counters rotate over three slots: step s appends to slot s % 3 and clears
 // slot (s + 1) % 3, which nobody reads during step s (it was last read right
 // after the barrier that ended step s - 2).
 struct alignas(128) Ctl {
-    unsigned long long bar;  // grid barrier arrivals (monotone)
+    unsigned long long bar;    // grid barrier arrivals (monotone)
     int32_t pad_bar[30];
-    int32_t qcnt[3];         // columns appended during a step
-    int32_t ecnt[3];         // endpoints appended during a step
-    int32_t err;             // first error code (0 = none)
-    int32_t status;          // final status of the launch
-    int32_t card;            // |M| at the end
+    unsigned long long epoch;  // grid barrier releases (monotone)
+    int32_t pad_epoch[30];
+    int32_t qcnt[3];           // columns appended during a step
+    int32_t ecnt[3];           // endpoints appended during a step (init: free columns)
+    int32_t tcnt[3];           // tiles handed out during a step
+    int32_t err;               // first error code (0 = none)
+    int32_t status;            // final status of the launch
+    int32_t card;              // |M| at the end
     int32_t initial_card;
     int32_t phases;
     int32_t n_endpoints_last;  // endpoints of the last BFS (inspection)
-    int32_t pad1[18];
+    int32_t pad1[15];
     long long levels;
     long long max_levels;
     long long cols_expanded;
@@ -86,6 +96,21 @@ struct Params {
     long long total_ns;  // limit of the whole launch
 };
 
+// Per-block shared state of the steps.
+struct Smem {
+    int tile;
+    int qn;     // entries in qbuf (may exceed QBUF: the excess went straight to global memory)
+    int qbase;  // global position of the flushed buffer
+    int total;  // edges of the current tile
+    int bc_a, bc_b, ok;  // barrier broadcast
+    int wsum[32];
+    int off[MAX_BLOCK];  // exclusive prefix of the tile's degrees
+    int beg[MAX_BLOCK];  // first edge of each tile column
+    int col[MAX_BLOCK];
+    int root[MAX_BLOCK];
+    int qbuf[QBUF];
+};
+
 // ------------------------------------------------------------------ memory helpers
 __device__ __forceinline__ int ld_volatile(const int32_t* p) {
     int v;
@@ -100,6 +125,9 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -109,7 +137,7 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 __device__ __forceinline__ void set_error(Ctl* ctl, int code) { atomicCAS(&ctl->err, 0, code); }
 
 // Appends v at base + (running count of `slot`) with one atomic per group of
-// converged lanes.
+// converged lanes (used for the rare endpoint appends and buffer overflow).
 __device__ __forceinline__ void push(int32_t* buf, int base, int32_t* slot, int v) {
     cg::coalesced_group g = cg::coalesced_threads();
     int pos = 0;
@@ -118,33 +146,93 @@ __device__ __forceinline__ void push(int32_t* buf, int base, int32_t* slot, int 
     buf[base + pos] = v;
 }
 
+// Appends a column to the block's buffer (global fallback when it is full).
+__device__ __forceinline__ void push_block(const Params& p, Smem& sm, int qbase, int slot, int v) {
+    const int pos = atomicAdd(&sm.qn, 1);
+    if (pos < QBUF) sm.qbuf[pos] = v;
+    else push(p.queue, qbase, &p.ctl->qcnt[slot], v);
+}
+
+// Writes the block's buffer to queue[qbase + ...] with one global atomic.
+// Called by all threads of the block.
+__device__ __forceinline__ void flush_block(const Params& p, Smem& sm, int qbase, int slot) {
+    __syncthreads();
+    const int n = min(sm.qn, QBUF);
+    if (n > 0 && threadIdx.x == 0) sm.qbase = atomicAdd(&p.ctl->qcnt[slot], n);
+    __syncthreads();
+    if (n > 0) {
+        const int b = qbase + sm.qbase;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) p.queue[b + k] = sm.qbuf[k];
+    }
+    if (threadIdx.x == 0) sm.qn = 0;  // the next write to qbuf/qn is behind a __syncthreads
+}
+
+// Block-wide exclusive prefix sum of v; returns this thread's offset and puts
+// the block total in sm.total.  Contains two __syncthreads.
+__device__ __forceinline__ int block_exclusive_scan(int v, Smem& sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    int incl = v;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        int t = __shfl_up_sync(FULL, incl, s);
+        if (lane >= s) incl += t;
+    }
+    if (lane == 31) sm.wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nwarps ? sm.wsum[lane] : 0;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            int t = __shfl_up_sync(FULL, w, s);
+            if (lane >= s) w += t;
+        }
+        sm.wsum[lane] = w;  // inclusive prefix of warp totals
+        if (lane == 31) sm.total = w;
+    }
+    __syncthreads();
+    return (warp > 0 ? sm.wsum[warp - 1] : 0) + incl - v;
+}
+
 // ------------------------------------------------------------------ grid barrier
-// All blocks of a cooperative launch.  Returns false (in every thread of the
-// block) when the wait ran out of time, the launch deadline passed or any
-// block recorded an error; the caller then leaves the kernel.
+// All blocks of a cooperative launch.  Arrivals count up one word; the last
+// arriver publishes the new epoch on another word, which the others poll.
+// If a_ptr/b_ptr are given, thread 0 reads them after the barrier and the
+// values are returned through sm.bc_a / sm.bc_b (one read per block instead of
+// one per thread).  Returns false (in every thread of the block) when the
+// wait ran out of time, the launch deadline passed or any block recorded an
+// error; the caller then leaves the kernel.
 __device__ __noinline__ bool grid_sync(Ctl* ctl, unsigned long long& target, long long wait_ns,
-                                       unsigned long long deadline) {
-    __shared__ int s_ok;
+                                       unsigned long long deadline, Smem& sm,
+                                       const int32_t* a_ptr, const int32_t* b_ptr) {
     __syncthreads();
     target += gridDim.x;
     if (threadIdx.x == 0) {
         int ok = 1;
         __threadfence();
-        atomicAdd(&ctl->bar, 1ull);
-        unsigned long long t_end = globaltimer() + (unsigned long long)wait_ns;
-        if (t_end > deadline) t_end = deadline;
-        unsigned spins = 0;
-        while (ld_acquire_u64(&ctl->bar) < target) {
-            if ((++spins & 31u) == 0) {
-                if (ld_volatile(&ctl->err) != 0) { ok = 0; break; }
-                if (globaltimer() > t_end) { set_error(ctl, -5 /*BM_ERR_TIMEOUT*/); ok = 0; break; }
+        const unsigned long long prev = atomicAdd(&ctl->bar, 1ull);
+        if (prev + 1 == target) {
+            __threadfence();
+            st_release_u64(&ctl->epoch, target);
+        } else {
+            unsigned long long t_end = globaltimer() + (unsigned long long)wait_ns;
+            if (t_end > deadline) t_end = deadline;
+            unsigned spins = 0;
+            while (ld_acquire_u64(&ctl->epoch) < target) {
+                if ((++spins & 15u) == 0) {
+                    if (ld_volatile(&ctl->err) != 0) { ok = 0; break; }
+                    if (globaltimer() > t_end) { set_error(ctl, -5 /*BM_ERR_TIMEOUT*/); ok = 0; break; }
+                }
             }
+            __threadfence();
         }
         if (ok && ld_volatile(&ctl->err) != 0) ok = 0;
-        s_ok = ok;
+        if (a_ptr) sm.bc_a = ld_volatile(a_ptr);
+        if (b_ptr) sm.bc_b = ld_volatile(b_ptr);
+        sm.ok = ok;
     }
     __syncthreads();
-    return s_ok != 0;
+    return sm.ok != 0;
 }
 
 struct Counters {
@@ -154,17 +242,17 @@ struct Counters {
 // ------------------------------------------------------------------ InitBfsArray
 // Algorithm 1 InitBfsArray (+ GPUBFS-WR root init, Section 3): level L0 for
 // unmatched columns, L0 - 1 for matched ones; root[c] = c for unmatched ones
-// (-1 otherwise: 0 is a valid column id).  Unmatched columns form the first
-// queue segment.  Before that, the column half of FixMatching: a column whose
+// (-1 otherwise: 0 is a valid column id).  Unmatched columns with at least one
+// row form the first queue segment (a column without rows can never be
+// matched, so it is not searched from); all unmatched columns are counted in
+// ecnt[slot].  Before that, the column half of FixMatching: a column whose
 // row does not point back is unmatched (the row half runs after Alternate).
 template <bool WR>
-__device__ __forceinline__ void step_init(const Params& p, int slot, Counters& cnt) {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nthr = gridDim.x * blockDim.x;
+__device__ __forceinline__ void step_init(const Params& p, int slot, Counters& cnt, Smem& sm) {
     const int nc = p.nc;
-    for (int base = tid - (tid & 31); base < nc; base += nthr) {  // warp-uniform trip count
-        int c = base + (threadIdx.x & 31);
-        bool is_free = false;
+    int nfree = 0;
+    for (int base = blockIdx.x * blockDim.x; base < nc; base += gridDim.x * blockDim.x) {  // block-uniform
+        const int c = base + threadIdx.x;
         if (c < nc) {
             int r = __ldcg(&p.cmatch[c]);
             if (r >= 0 && __ldcg(&p.rmatch[r]) != c) {
@@ -172,61 +260,44 @@ __device__ __forceinline__ void step_init(const Params& p, int slot, Counters& c
                 r = -1;
                 cnt.fixes++;
             }
-            is_free = (r < 0);
+            const bool is_free = (r < 0);
             __stcg(&p.level[c], is_free ? L0 : L0 - 1);
             if (WR) __stcg(&p.root[c], is_free ? c : -1);
+            if (is_free) {
+                ++nfree;
+                if (__ldg(&p.col_ptr[c + 1]) > __ldg(&p.col_ptr[c])) push_block(p, sm, 0, slot, c);
+            }
         }
-        if (is_free) push(p.queue, 0, &p.ctl->qcnt[slot], c);
+        flush_block(p, sm, 0, slot);
     }
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) nfree += __shfl_down_sync(FULL, nfree, s);
+    if ((threadIdx.x & 31) == 0 && nfree) atomicAdd(&p.ctl->ecnt[slot], nfree);
 }
 
 // ------------------------------------------------------------------ BFS level
-// Visits edge (row r, column c) of a column c at level lvl whose search tree
-// has root `myroot` (GPUBFS-WR).  Algorithm 2 / 4, loop body.
-template <bool WR>
-__device__ __forceinline__ void visit(const Params& p, int r, int c, int myroot, int lvl,
-                                      int qbase, int qslot, int ebase, int eslot, Counters& cnt) {
-    int cm = __ldcg(&p.rmatch[r]);
-    if (cm >= 0) {
-        cnt.em++;
-        // matched row: its column joins the next level unless already reached
-        if (__ldcg(&p.level[cm]) == L0 - 1 && atomicCAS(&p.level[cm], L0 - 1, lvl + 1) == L0 - 1) {
-            __stcg(&p.pred[r], c);
-            if (WR) __stcg(&p.root[cm], myroot);
-            push(p.queue, qbase, &p.ctl->qcnt[qslot], cm);
-        }
-    } else if (cm == -1) {
-        // unmatched row: an augmenting path ends here
-        if (WR && p.one_ep) {
-            if (__ldcg(&p.level[myroot]) == L0 && atomicCAS(&p.rmatch[r], -1, -2) == -1) {
-                if (atomicCAS(&p.level[myroot], L0, -r) == L0) {
-                    __stcg(&p.pred[r], c);
-                    push(p.endpoints, ebase, &p.ctl->ecnt[eslot], r);
-                } else {
-                    atomicExch(&p.rmatch[r], -1);  // root served meanwhile: give the row back
-                }
-            }
-        } else if (atomicCAS(&p.rmatch[r], -1, -2) == -1) {
-            if (WR) __stcg(&p.level[myroot], L0 - 2);
-            __stcg(&p.pred[r], c);
-            push(p.endpoints, ebase, &p.ctl->ecnt[eslot], r);
-        }
-    }
-}
-
-// Expands the queue segment [qb, qe) whose columns are at level lvl.  New
-// columns are appended at qe + (slot count), endpoints at ebase + (slot count).
+// Expands the queue segment [qb, qe) whose columns are at level lvl
+// (Algorithm 2 / 4 loop body for every edge of every column).  New columns
+// are appended at qe + (slot count), endpoints at ebase + (slot count).
 template <bool WR>
 __device__ __forceinline__ void step_expand(const Params& p, int qb, int qe, int lvl, int slot,
-                                            int ebase, Counters& cnt) {
-    const int lane = threadIdx.x & 31;
-    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+                                            int ebase, Counters& cnt, Smem& sm) {
     const int q = qe - qb;
-    for (int base = gwarp * 32; base < q; base += nwarps * 32) {  // warp-uniform
-        const int i = base + lane;
+    const int T = blockDim.x;
+    // tile width: spread small frontiers over many blocks, never above blockDim
+    int tw = (q + gridDim.x - 1) / gridDim.x;
+    tw = (tw + 31) & ~31;
+    if (tw > T) tw = T;
+    if (tw < 32) tw = 32;
+    const int ntiles = (q + tw - 1) / tw;
+    int tile = blockIdx.x;
+    for (;;) {
+        if (tile >= ntiles) break;  // block-uniform
+        // ---- load the tile's columns: one per thread (threads >= tw idle here)
+        const int t = threadIdx.x;
+        const int i = tile * tw + t;
         int c = -1, beg = 0, deg = 0, myroot = -1;
-        if (i < q) {
+        if (t < tw && i < q) {
             c = __ldcg(&p.queue[qb + i]);
             if (WR) {
                 myroot = __ldcg(&p.root[c]);
@@ -238,50 +309,73 @@ __device__ __forceinline__ void step_expand(const Params& p, int qb, int qe, int
                 cnt.cols++;
             }
         }
-        // columns with more than 32 rows: the whole warp scans one at a time
-        unsigned big = __ballot_sync(FULL, deg > 32);
-        while (big) {
-            const int src = __ffs(big) - 1;
-            big &= big - 1;
-            const int bc = __shfl_sync(FULL, c, src);
-            const int bb = __shfl_sync(FULL, beg, src);
-            const int bd = __shfl_sync(FULL, deg, src);
-            const int br = __shfl_sync(FULL, myroot, src);
-            int j0 = 0;
-            for (; j0 < bd; j0 += 32) {
-                if (WR && j0 != 0 && (j0 & 255) == 0) {  // re-check the root every 256 rows
-                    if (__ldcg(&p.level[br]) < L0 - 1) break;
+        const int off = block_exclusive_scan(deg, sm);
+        sm.off[t] = off;
+        sm.beg[t] = beg;
+        sm.col[t] = c;
+        sm.root[t] = myroot;
+        if (t == 0) sm.tile = gridDim.x + atomicAdd(&p.ctl->tcnt[slot], 1);
+        __syncthreads();
+        const int total = sm.total;
+        const int next_tile = sm.tile;
+        cnt.edges += (t == 0) ? total : 0;
+        // ---- edges of the tile, ILP per thread
+        for (int e0 = 0; e0 < total; e0 += T * ILP) {
+            int own[ILP], r[ILP], cm[ILP], lv[ILP];
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) {
+                const int e = e0 + u * T + t;
+                own[u] = -1;
+                r[u] = -1;
+                if (e < total) {
+                    int lo = 0, hi = tw - 1;  // last k with off[k] <= e
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (sm.off[mid] <= e) lo = mid; else hi = mid - 1;
+                    }
+                    own[u] = lo;
+                    r[u] = __ldg(&p.row_idx[sm.beg[lo] + (e - sm.off[lo])]);
                 }
-                const int j = j0 + lane;
-                if (j < bd) visit<WR>(p, __ldg(&p.row_idx[bb + j]), bc, br, lvl, qe, slot, ebase, slot, cnt);
             }
-            if (lane == 0) cnt.edges += (j0 < bd ? j0 : bd);
-        }
-        if (deg > 32) deg = 0;
-        // the rest: warp-wide prefix sum of degrees, one edge per lane per pass
-        int incl = deg;
 #pragma unroll
-        for (int s = 1; s < 32; s <<= 1) {
-            int v = __shfl_up_sync(FULL, incl, s);
-            if (lane >= s) incl += v;
-        }
-        const int total = __shfl_sync(FULL, incl, 31);
-        const int off = incl - deg;
-        if (lane == 0) cnt.edges += total;
-        for (int k = 0; k < total; k += 32) {
-            const int e = k + lane;
-            int owner = 0;  // last lane whose range starts at or before e
+            for (int u = 0; u < ILP; ++u) cm[u] = (own[u] >= 0) ? __ldcg(&p.rmatch[r[u]]) : -3;
 #pragma unroll
-            for (int s = 16; s >= 1; s >>= 1) {
-                int o = __shfl_sync(FULL, off, owner + s);
-                if (o <= e) owner += s;
+            for (int u = 0; u < ILP; ++u) lv[u] = (cm[u] >= 0) ? __ldcg(&p.level[cm[u]]) : 0;
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) {
+                if (own[u] < 0) continue;
+                const int col = sm.col[own[u]];
+                const int rt = sm.root[own[u]];
+                if (cm[u] >= 0) {
+                    cnt.em++;
+                    // matched row: its column joins the next level unless already reached
+                    if (lv[u] == L0 - 1 && atomicCAS(&p.level[cm[u]], L0 - 1, lvl + 1) == L0 - 1) {
+                        __stcg(&p.pred[r[u]], col);
+                        if (WR) __stcg(&p.root[cm[u]], rt);
+                        push_block(p, sm, qe, slot, cm[u]);
+                    }
+                } else if (cm[u] == -1) {
+                    // unmatched row: an augmenting path ends here
+                    const int row = r[u];
+                    if (WR && p.one_ep) {
+                        if (__ldcg(&p.level[rt]) == L0 && atomicCAS(&p.rmatch[row], -1, -2) == -1) {
+                            if (atomicCAS(&p.level[rt], L0, -row) == L0) {
+                                __stcg(&p.pred[row], col);
+                                push(p.endpoints, ebase, &p.ctl->ecnt[slot], row);
+                            } else {
+                                atomicExch(&p.rmatch[row], -1);  // root served meanwhile: give the row back
+                            }
+                        }
+                    } else if (atomicCAS(&p.rmatch[row], -1, -2) == -1) {
+                        if (WR) __stcg(&p.level[rt], L0 - 2);
+                        __stcg(&p.pred[row], col);
+                        push(p.endpoints, ebase, &p.ctl->ecnt[slot], row);
+                    }
+                }
             }
-            const int oc = __shfl_sync(FULL, c, owner);
-            const int ob = __shfl_sync(FULL, beg, owner);
-            const int oo = __shfl_sync(FULL, off, owner);
-            const int orr = __shfl_sync(FULL, myroot, owner);
-            if (e < total) visit<WR>(p, __ldg(&p.row_idx[ob + (e - oo)]), oc, orr, lvl, qe, slot, ebase, slot, cnt);
         }
+        flush_block(p, sm, qe, slot);
+        tile = next_tile;
     }
 }
 

@@ -23,6 +23,7 @@ using bmd::Counters;
 using bmd::Ctl;
 using bmd::L0;
 using bmd::Params;
+using bmd::Smem;
 
 namespace {
 
@@ -36,6 +37,8 @@ template <bool WR>
 __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
     using namespace bmd;
     Ctl* ctl = p.ctl;
+    __shared__ Smem sm;
+    if (threadIdx.x == 0) sm.qn = 0;
     unsigned long long target = 0;
     const unsigned long long t_start = globaltimer();
     const unsigned long long deadline = t_start + (unsigned long long)p.total_ns;
@@ -51,11 +54,11 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
     for (;;) {
         // ---- InitBfsArray (+ column half of FixMatching)
         int s = step++;
-        if (leader) { ctl->qcnt[(s + 1) % 3] = 0; ctl->ecnt[(s + 1) % 3] = 0; }
-        step_init<WR>(p, s % 3, cnt);
-        if (!grid_sync(ctl, target, p.wait_ns, deadline)) goto out;
-        const int n_roots = ld_volatile(&ctl->qcnt[s % 3]);
-        card = p.nc - n_roots;
+        if (leader) { ctl->qcnt[(s + 1) % 3] = 0; ctl->ecnt[(s + 1) % 3] = 0; ctl->tcnt[(s + 1) % 3] = 0; }
+        step_init<WR>(p, s % 3, cnt, sm);
+        if (!grid_sync(ctl, target, p.wait_ns, deadline, sm, &ctl->qcnt[s % 3], &ctl->ecnt[s % 3])) goto out;
+        const int n_roots = sm.bc_a;  // unmatched columns with rows: the first queue segment
+        card = p.nc - sm.bc_b;        // all unmatched columns
         if (leader && phases == 0) ctl->initial_card = card;
         if (n_roots == 0) break;  // every column matched
         if (phases >= p.max_phases) {
@@ -68,11 +71,11 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
         int qb = 0, qe = n_roots, lvl = L0, n_ep = 0, levels = 0;
         for (;;) {
             int s2 = step++;
-            if (leader) { ctl->qcnt[(s2 + 1) % 3] = 0; ctl->ecnt[(s2 + 1) % 3] = 0; }
-            step_expand<WR>(p, qb, qe, lvl, s2 % 3, n_ep, cnt);
-            if (!grid_sync(ctl, target, p.wait_ns, deadline)) goto out;
-            const int nq = ld_volatile(&ctl->qcnt[s2 % 3]);
-            n_ep += ld_volatile(&ctl->ecnt[s2 % 3]);
+            if (leader) { ctl->qcnt[(s2 + 1) % 3] = 0; ctl->ecnt[(s2 + 1) % 3] = 0; ctl->tcnt[(s2 + 1) % 3] = 0; }
+            step_expand<WR>(p, qb, qe, lvl, s2 % 3, n_ep, cnt, sm);
+            if (!grid_sync(ctl, target, p.wait_ns, deadline, sm, &ctl->qcnt[s2 % 3], &ctl->ecnt[s2 % 3])) goto out;
+            const int nq = sm.bc_a;
+            n_ep += sm.bc_b;
             ++levels;
             ins_total += nq;
             if (nq == 0) break;                  // no vertex inserted
@@ -88,16 +91,16 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
 
         if (p.bfs_only) {
             step_release_endpoints(p, n_ep);
-            if (!grid_sync(ctl, target, p.wait_ns, deadline)) goto out;
+            if (!grid_sync(ctl, target, p.wait_ns, deadline, sm, nullptr, nullptr)) goto out;
             break;
         }
         if (n_ep == 0) break;  // no augmenting path: the matching is maximum (Berge)
 
         // ---- Alternate, then the row half of FixMatching
         step_alternate(p, n_ep, levels + 2, cnt);
-        if (!grid_sync(ctl, target, p.wait_ns, deadline)) goto out;
+        if (!grid_sync(ctl, target, p.wait_ns, deadline, sm, nullptr, nullptr)) goto out;
         step_fix_rows(p, cnt);
-        if (!grid_sync(ctl, target, p.wait_ns, deadline)) goto out;
+        if (!grid_sync(ctl, target, p.wait_ns, deadline, sm, nullptr, nullptr)) goto out;
     }
 out:
     flush_counters(p, cnt);
@@ -117,14 +120,20 @@ out:
 // ---- per-step kernels of the host-driven loop (the paper's structure)
 template <bool WR>
 __global__ void __launch_bounds__(1024) k_init(Params p, int slot) {
+    __shared__ bmd::Smem sm;
+    if (threadIdx.x == 0) sm.qn = 0;
+    __syncthreads();
     Counters cnt{0, 0, 0, 0, 0};
-    bmd::step_init<WR>(p, slot, cnt);
+    bmd::step_init<WR>(p, slot, cnt, sm);
     bmd::flush_counters(p, cnt);
 }
 template <bool WR>
 __global__ void __launch_bounds__(1024) k_expand(Params p, int qb, int qe, int lvl, int slot, int ebase) {
+    __shared__ bmd::Smem sm;
+    if (threadIdx.x == 0) sm.qn = 0;
+    __syncthreads();
     Counters cnt{0, 0, 0, 0, 0};
-    bmd::step_expand<WR>(p, qb, qe, lvl, slot, ebase, cnt);
+    bmd::step_expand<WR>(p, qb, qe, lvl, slot, ebase, cnt, sm);
     bmd::flush_counters(p, cnt);
 }
 __global__ void __launch_bounds__(1024) k_alternate(Params p, int n_ep, int cap) {
@@ -345,6 +354,7 @@ int32_t run_host_loop(bm_ctx* ctx, const Params& p) {
     auto clear_slot = [&](int slot) -> int32_t {
         BM_CUDA(ctx, cudaMemsetAsync(&ctx->ctl->qcnt[slot], 0, sizeof(int32_t), st));
         BM_CUDA(ctx, cudaMemsetAsync(&ctx->ctl->ecnt[slot], 0, sizeof(int32_t), st));
+        BM_CUDA(ctx, cudaMemsetAsync(&ctx->ctl->tcnt[slot], 0, sizeof(int32_t), st));
         return BM_OK;
     };
     int32_t rc = sync_ctl(ctx);
@@ -357,7 +367,7 @@ int32_t run_host_loop(bm_ctx* ctx, const Params& p) {
         BM_CUDA(ctx, cudaGetLastError());
         if ((rc = sync_ctl(ctx))) return rc;
         const int n_roots = h->qcnt[s % 3];
-        card = p.nc - n_roots;
+        card = p.nc - h->ecnt[s % 3];
         if (phases == 0) {
             BM_CUDA(ctx, cudaMemcpyAsync(&ctx->ctl->initial_card, &card, sizeof(int), cudaMemcpyHostToDevice, st));
         }
