@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--workload", default="rmat21", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -243,6 +244,112 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ batched workload
+BATCH_WORKLOAD = ("4,096 uniform random bipartite graphs, rows log-uniform in [100, 50,000], "
+                  "columns = rows x U[0.8, 1.25], column degree U{1..round(2mu-1)} with mu ~ "
+                  "U[2, 12], concatenated int32 CSR with int64 offsets, seed 3; greedy "
+                  "initial matching inside the launch")
+
+
+def bench_batched(args, torch, bmatch, stream, flush):
+    """Batched graphs/s (one persistent launch, geometry from the autotuner)
+    against the single-graph path called once per graph on the same stream."""
+    from paper_1303_1379_gb300 import synth
+    t_gen = time.perf_counter()
+    b = synth.batch_graphs(4096, seed=3)
+    t_gen = time.perf_counter() - t_gen
+    G = b.n_graphs
+    R, C, E = int(b.row_off[-1]), int(b.col_off[-1]), int(b.edge_off[-1])
+    bb = bmatch.Batch.from_synth(b, stream=stream.cuda_stream)
+    dev = bb.col_ptr.device
+    rm0 = torch.full((R,), -1, dtype=torch.int32, device=dev)
+    cm0 = torch.full((C,), -1, dtype=torch.int32, device=dev)
+    rm, cm = torch.empty_like(rm0), torch.empty_like(cm0)
+    card = torch.zeros(G, dtype=torch.int32, device=dev)
+    cands = [(256, 4), (256, 2), (512, 2), (512, 1), (1024, 1)]
+    best, tune_ms = bb.autotune(rm0, cm0, rm, cm, cands, greedy=True, reps=2)
+    times = []
+    for i in range(args.warmup + args.steps):
+        rm.copy_(rm0)
+        cm.copy_(cm0)
+        flush.fill_(i)
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, st = bb.match(rm, cm, greedy=True, card_out=card)
+        z.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            times.append(a.elapsed_time(z))
+    batch_ms = statistics.mean(times)
+    batch_cards = card.cpu().numpy().copy()
+    # one by one: the plain single-graph path, one context per graph (made untimed)
+    ctxs = []
+    cp_base, ri_base = bb.col_ptr.data_ptr(), bb.row_idx.data_ptr()
+    for k in range(G):
+        ctxs.append(bmatch.Matcher(int(b.n_rows[k]), int(b.n_cols[k]),
+                                   int(b.edge_off[k + 1] - b.edge_off[k]),
+                                   cp_base + 4 * int(b.col_off[k] + k),
+                                   ri_base + 4 * int(b.edge_off[k]), stream=stream.cuda_stream))
+    one = []
+    ok = True
+    for rep in range(2):
+        flush.fill_(rep)
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k, m in enumerate(ctxs):
+            m.set_matching(None, None)
+            m.greedy()
+            r = m.match()
+            if rep == 0 and r.card != int(batch_cards[k]):
+                ok = False
+        z.record(stream)
+        torch.cuda.synchronize()
+        one.append(a.elapsed_time(z))
+    for m in ctxs:
+        m.close()
+    one_ms = min(one)
+    bb.close()
+    return {
+        "workload": BATCH_WORKLOAD, "graphs": G, "rows": R, "cols": C, "edges": E,
+        "generate_s": round(t_gen, 2),
+        "ms": batch_ms, "graphs_per_s": G / (batch_ms * 1e-3),
+        "gteps": E / (batch_ms * 1e-3) / 1e9,
+        "one_by_one_ms": one_ms, "one_by_one_graphs_per_s": G / (one_ms * 1e-3),
+        "speedup_vs_one_by_one": one_ms / batch_ms,
+        "same_cardinalities_as_one_by_one": ok,
+        "autotune": {"candidates": cands, "ms": tune_ms, "chosen": cands[best]},
+        "phases": st["phases"], "levels": st["levels"],
+    }, b, batch_cards
+
+
+def batched_cpu_baseline(b, batch_cards):
+    """Oracle (greedy + Hopcroft-Karp, all host threads) on a seeded sample of
+    the batch; also checks the GPU cardinalities of the sample."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(3)
+    idx = np.sort(rng.choice(b.n_graphs, size=256, replace=False))
+    from paper_1303_1379_gb300.synth import Batch
+    nr, nc = b.n_rows[idx], b.n_cols[idx]
+    ro = np.zeros(len(idx) + 1, np.int64); np.cumsum(nr, out=ro[1:])
+    co = np.zeros(len(idx) + 1, np.int64); np.cumsum(nc, out=co[1:])
+    cps, ris, eo = [], [], [0]
+    for k in idx:
+        g = b.graph(int(k))
+        cps.append(g.col_ptr)
+        ris.append(g.row_idx)
+        eo.append(eo[-1] + g.nnz)
+    sub = Batch(nr, nc, ro, co, np.array(eo, np.int64), np.concatenate(cps), np.concatenate(ris))
+    t = time.perf_counter()
+    _, _, cards = oracle.hk_batch(sub, greedy_first=True)
+    dt = time.perf_counter() - t
+    agree = bool(np.array_equal(cards, batch_cards[idx]))
+    return {"value": len(idx) / dt, "unit": "graphs/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"256 seeded graphs of the batch, greedy + Hopcroft-Karp "
+            f"over all host threads ({dt:.1f} s)", "cardinalities_agree": agree}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import numpy as np
@@ -385,6 +492,11 @@ def run_ours(args):
                          f"({tmed * 1e3:.0f} ms each)"}
 
     m.close()
+    batched = None
+    if not args.no_batch:
+        batched, bgraphs, bcards = bench_batched(args, torch, bmatch, stream, flush)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            batched["cpu_baseline"] = batched_cpu_baseline(bgraphs, bcards)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -410,6 +522,7 @@ def run_ours(args):
                      "algorithmic_bytes": alg_bytes, "peak_kind": peak_kind},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "batched": batched,
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
         "wall_s": wall,

@@ -207,8 +207,93 @@ BM_API int32_t bm_match_host(bm_ctx *ctx, const int32_t *h_col_ptr, const int32_
 BM_API int32_t bm_bfs(bm_ctx *ctx, int32_t *level_out, int32_t *root_out, int32_t *pred_out,
                int32_t *endpoints_out, int32_t *n_endpoints_out);
 
+/*
+ * Per-phase profile of the last bm_match on this context (the quantities of
+ * Fig. 2 of the paper: BFS levels -- kernel calls in the paper's host loop --
+ * of every outer iteration of Algorithm 1).  For each of the first
+ * min(cap, phases, 4096) phases that searched: levels[i], endpoints[i] (rows
+ * claimed), first_ep_level[i] / last_ep_level[i] (1-based level at which the
+ * first / last endpoint was claimed, 0 if none).  Host arrays, each nullable;
+ * *n_out gets the number of entries written.
+ */
+BM_API int32_t bm_phase_profile(bm_ctx *ctx, int32_t cap, int32_t *levels, int32_t *endpoints,
+                                int32_t *first_ep_level, int32_t *last_ep_level, int32_t *n_out);
+
 /* Releases the context and its workspace (never the caller's buffers). */
 BM_API int32_t bm_destroy(bm_ctx *ctx);
+
+/* ------------------------------------------------------------------ batches
+ * Many independent graphs matched by ONE persistent launch (the paper's
+ * method per graph; the batching is this library's addition, for solvers that
+ * match many matrices or diagonal blocks).  Each block of the launch runs the
+ * whole method on one graph at a time, taking graphs largest first from an
+ * atomic counter; graphs never wait for each other.  The launch is recorded in
+ * a CUDA graph once and replayed by every bm_batch_match.
+ */
+typedef struct bm_batch_desc {
+    int32_t n_graphs;
+    int32_t reserved0;
+    const int32_t *n_rows;    /* device [n_graphs]                                        */
+    const int32_t *n_cols;    /* device [n_graphs]                                        */
+    const int64_t *row_off;   /* device [n_graphs+1], from 0: graph k's rows are entries
+                                 row_off[k] .. row_off[k+1]-1 of the batch rmatch         */
+    const int64_t *col_off;   /* device [n_graphs+1], from 0: its columns in cmatch       */
+    const int64_t *edge_off;  /* device [n_graphs+1], from 0: its edges in row_idx        */
+    const int32_t *col_ptr;   /* device: graph k's own col_ptr (n_cols[k]+1 entries, from
+                                 0) starts at col_ptr + col_off[k] + k                    */
+    const int32_t *row_idx;   /* device: graph k's rows, local ids in [0, n_rows[k])      */
+} bm_batch_desc;
+
+typedef struct bm_batch_stats {
+    int32_t status;            /* first non-zero per-graph status, else 0                  */
+    int32_t grid, block;       /* launch geometry used                                     */
+    int32_t reserved0;
+    int64_t phases, levels, columns_expanded, edges_scanned, endpoints, fix_repairs,
+            alternate_steps;   /* sums over the graphs                                     */
+    int64_t reserved[4];
+} bm_batch_stats;
+
+typedef struct bm_batch bm_batch;
+
+/* Creates a batch over the graphs described by *desc (device arrays borrowed
+ * until bm_batch_destroy).  Reads the three offset arrays back once (to size
+ * the workspace and order the graphs by edge count), validates every graph's
+ * CSR on the device (BM_ERR_INVALID_CSR) and allocates the workspace (about
+ * 12 bytes per column and 8 per row of the whole batch).  opt: mode, bfs,
+ * wr_one_endpoint, block_size, blocks_per_sm are used; NULL = defaults. */
+BM_API int32_t bm_batch_create(const bm_batch_desc *desc, void *stream, const bm_options *opt,
+                               bm_batch **out);
+
+/* Changes mode / BFS kind / launch geometry (the next match re-records the launch). */
+BM_API int32_t bm_batch_set_options(bm_batch *b, const bm_options *opt);
+
+/* Matches every graph.  rmatch / cmatch: device arrays over the whole batch
+ * (row_off / col_off slices, local ids), the initial matchings on entry (-1
+ * for none) and the maximum matchings on return.  greedy != 0 first runs the
+ * cheap matching of Section 4 inside the launch.  card_out: device
+ * [n_graphs] (nullable) gets each |M|.  Returns the first per-graph error (see
+ * bm_batch_graph_status) or BM_OK. */
+BM_API int32_t bm_batch_match(bm_batch *b, int32_t greedy, int32_t *rmatch, int32_t *cmatch,
+                              int32_t *card_out, bm_batch_stats *stats);
+
+/* Per-graph status and phase count of the last bm_batch_match (device arrays
+ * [n_graphs], each nullable). */
+BM_API int32_t bm_batch_graph_status(bm_batch *b, int32_t *status_out, int32_t *phases_out);
+
+/* Autotuner: times bm_batch_match (from the initial matching rmatch0 /
+ * cmatch0, copied into rmatch_work / cmatch_work before every run, all device
+ * arrays over the batch) for each candidate (block_sizes[i], blocks_per_sm[i])
+ * and keeps the fastest as the batch's launch geometry.  ms_out[i] (host,
+ * nullable) gets the best of `reps` runs of candidate i (negative if it cannot
+ * launch); *best_out (host) the chosen index. */
+BM_API int32_t bm_batch_autotune(bm_batch *b, int32_t greedy, const int32_t *rmatch0,
+                                 const int32_t *cmatch0, int32_t *rmatch_work,
+                                 int32_t *cmatch_work, int32_t n_candidates,
+                                 const int32_t *block_sizes, const int32_t *blocks_per_sm,
+                                 int32_t reps, float *ms_out, int32_t *best_out);
+
+/* Releases the batch's workspace (never the caller's buffers). */
+BM_API int32_t bm_batch_destroy(bm_batch *b);
 
 /*
  * Allocation-free matching (no counterpart in the paper; an addition for

@@ -32,9 +32,31 @@ BM_APFB, BM_APSB = 0, 1
 BM_GPUBFS, BM_GPUBFS_WR = 0, 1
 BM_DRIVER_PERSISTENT, BM_DRIVER_HOST = 0, 1
 
+class bm_batch_desc(ctypes.Structure):
+    _fields_ = [("n_graphs", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("n_rows", ctypes.c_void_p), ("n_cols", ctypes.c_void_p),
+                ("row_off", ctypes.c_void_p), ("col_off", ctypes.c_void_p),
+                ("edge_off", ctypes.c_void_p), ("col_ptr", ctypes.c_void_p),
+                ("row_idx", ctypes.c_void_p)]
+
+
+class bm_batch_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("phases", ctypes.c_int64),
+                ("levels", ctypes.c_int64), ("columns_expanded", ctypes.c_int64),
+                ("edges_scanned", ctypes.c_int64), ("endpoints", ctypes.c_int64),
+                ("fix_repairs", ctypes.c_int64), ("alternate_steps", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 4)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
 EXPORTS = ("bm_default_options", "bm_version", "bm_status_string", "bm_create", "bm_upload_csr",
            "bm_set_options", "bm_greedy", "bm_set_matching", "bm_get_matching", "bm_match",
-           "bm_match_host", "bm_bfs", "bm_destroy")
+           "bm_match_host", "bm_bfs", "bm_phase_profile", "bm_destroy", "bm_batch_create",
+           "bm_batch_set_options", "bm_batch_match", "bm_batch_graph_status", "bm_batch_autotune",
+           "bm_batch_destroy", "bm_match_noalloc")
 
 
 class bm_options(ctypes.Structure):
@@ -111,6 +133,24 @@ def load(build_if_missing: bool = True):
             lib.bm_match_host.restype = ctypes.c_int32
             lib.bm_bfs.argtypes = [VP, VP, VP, VP, VP, I32P]
             lib.bm_bfs.restype = ctypes.c_int32
+            lib.bm_phase_profile.argtypes = [VP, ctypes.c_int32, I32P, I32P, I32P, I32P, I32P]
+            lib.bm_phase_profile.restype = ctypes.c_int32
+            lib.bm_batch_create.argtypes = [ctypes.POINTER(bm_batch_desc), VP,
+                                            ctypes.POINTER(bm_options), ctypes.POINTER(VP)]
+            lib.bm_batch_create.restype = ctypes.c_int32
+            lib.bm_batch_set_options.argtypes = [VP, ctypes.POINTER(bm_options)]
+            lib.bm_batch_set_options.restype = ctypes.c_int32
+            lib.bm_batch_match.argtypes = [VP, ctypes.c_int32, VP, VP, VP,
+                                           ctypes.POINTER(bm_batch_stats)]
+            lib.bm_batch_match.restype = ctypes.c_int32
+            lib.bm_batch_graph_status.argtypes = [VP, VP, VP]
+            lib.bm_batch_graph_status.restype = ctypes.c_int32
+            lib.bm_batch_autotune.argtypes = [VP, ctypes.c_int32, VP, VP, VP, VP, ctypes.c_int32,
+                                              I32P, I32P, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_float), I32P]
+            lib.bm_batch_autotune.restype = ctypes.c_int32
+            lib.bm_batch_destroy.argtypes = [VP]
+            lib.bm_batch_destroy.restype = ctypes.c_int32
             lib.bm_destroy.argtypes = [VP]
             lib.bm_destroy.restype = ctypes.c_int32
             _lib = lib
@@ -256,6 +296,16 @@ class Matcher:
         _check(rc, "bm_match_host")
         return MatchResult(rc, card.value, st.as_dict())
 
+    def phase_profile(self, cap: int = 4096):
+        """Per-phase (levels, endpoints, first_ep_level, last_ep_level) of the
+        last match (Fig. 2 of the paper: BFS levels per outer iteration)."""
+        import numpy as np
+        arrs = [np.zeros(max(cap, 1), np.int32) for _ in range(4)]
+        n = ctypes.c_int32(0)
+        ptrs = [a.ctypes.data_as(I32P) for a in arrs]
+        _check(self._lib.bm_phase_profile(self._h, cap, *ptrs, ctypes.byref(n)), "bm_phase_profile")
+        return [a[:n.value] for a in arrs]
+
     def bfs(self, level_out=None, root_out=None, pred_out=None, endpoints_out=None) -> int:
         n = ctypes.c_int32(0)
         _check(self._lib.bm_bfs(self._h, _ptr(level_out), _ptr(root_out), _ptr(pred_out),
@@ -279,3 +329,97 @@ def bm_match_noalloc(n_rows: int, n_cols: int, nnz: int, col_ptr, row_idx, rmatc
     rc = fn(int(n_rows), int(n_cols), int(nnz), _ptr(col_ptr), _ptr(row_idx), _ptr(rmatch),
             _ptr(cmatch), st, ctypes.byref(card))
     return int(rc), card.value
+
+
+class Batch:
+    """One bm_batch: many graphs (see synth.Batch for the layout) matched by
+    one persistent launch.  The device copies of the descriptor arrays are
+    kept alive by this object."""
+
+    def __init__(self, n_rows, n_cols, row_off, col_off, edge_off, col_ptr, row_idx,
+                 stream: int | None = None, **options):
+        import torch
+        self._lib = load()
+        dev = torch.device("cuda", torch.cuda.current_device())
+
+        def d(x, dt):
+            return torch.as_tensor(x, dtype=dt).to(dev).contiguous()
+        self.n_rows = d(n_rows, torch.int32)
+        self.n_cols = d(n_cols, torch.int32)
+        self.row_off = d(row_off, torch.int64)
+        self.col_off = d(col_off, torch.int64)
+        self.edge_off = d(edge_off, torch.int64)
+        self.col_ptr = d(col_ptr, torch.int32)
+        self.row_idx = d(row_idx, torch.int32) if len(row_idx) else torch.zeros(1, dtype=torch.int32, device=dev)
+        self.n_graphs = int(self.n_rows.numel())
+        self.total_rows = int(row_off[-1])
+        self.total_cols = int(col_off[-1])
+        self.stream = _current_stream() if stream is None else stream
+        self.options = default_options(**options)
+        self.desc = bm_batch_desc(self.n_graphs, 0, self.n_rows.data_ptr(), self.n_cols.data_ptr(),
+                                  self.row_off.data_ptr(), self.col_off.data_ptr(),
+                                  self.edge_off.data_ptr(), self.col_ptr.data_ptr(),
+                                  self.row_idx.data_ptr())
+        h = VP()
+        _check(self._lib.bm_batch_create(ctypes.byref(self.desc), self.stream,
+                                         ctypes.byref(self.options), ctypes.byref(h)),
+               "bm_batch_create")
+        self._h = h
+
+    @classmethod
+    def from_synth(cls, b, **options):
+        return cls(b.n_rows, b.n_cols, b.row_off, b.col_off, b.edge_off, b.col_ptr, b.row_idx,
+                   **options)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_options(self, **options):
+        o = default_options(**{**{k: getattr(self.options, k) for k, _ in bm_options._fields_
+                                  if k != "reserved"}, **options})
+        _check(self._lib.bm_batch_set_options(self._h, ctypes.byref(o)), "bm_batch_set_options")
+        self.options = o
+
+    def match(self, rmatch, cmatch, greedy: bool = True, card_out=None):
+        """rmatch/cmatch: device int32 over the batch (initial -> maximum).
+        Returns (status, stats dict)."""
+        st = bm_batch_stats()
+        rc = self._lib.bm_batch_match(self._h, int(bool(greedy)), _ptr(rmatch), _ptr(cmatch),
+                                      _ptr(card_out), ctypes.byref(st))
+        _check(rc, "bm_batch_match")
+        return rc, st.as_dict()
+
+    def graph_status(self):
+        import torch
+        s = torch.empty(max(self.n_graphs, 1), dtype=torch.int32, device="cuda")
+        p = torch.empty(max(self.n_graphs, 1), dtype=torch.int32, device="cuda")
+        _check(self._lib.bm_batch_graph_status(self._h, _ptr(s), _ptr(p)), "bm_batch_graph_status")
+        return s[:self.n_graphs].cpu().numpy(), p[:self.n_graphs].cpu().numpy()
+
+    def autotune(self, rmatch0, cmatch0, rmatch_work, cmatch_work, candidates, greedy=True, reps=2):
+        """Times each (block_size, blocks_per_sm) candidate and keeps the
+        fastest.  Returns (best index, [ms per candidate])."""
+        n = len(candidates)
+        blocks = (ctypes.c_int32 * n)(*[c[0] for c in candidates])
+        bps = (ctypes.c_int32 * n)(*[c[1] for c in candidates])
+        ms = (ctypes.c_float * n)()
+        best = ctypes.c_int32(-1)
+        _check(self._lib.bm_batch_autotune(self._h, int(bool(greedy)), _ptr(rmatch0), _ptr(cmatch0),
+                                           _ptr(rmatch_work), _ptr(cmatch_work), n, blocks, bps,
+                                           reps, ms, ctypes.byref(best)), "bm_batch_autotune")
+        self.options.block_size, self.options.blocks_per_sm = candidates[best.value]
+        return best.value, list(ms)

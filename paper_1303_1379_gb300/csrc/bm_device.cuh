@@ -91,7 +91,8 @@ struct Params {
     int32_t max_phases;  // stop after this many phases (>= 1)
     int32_t phase_limit_is_error;
     int32_t bfs_only;    // run one BFS, no Alternate, leave the matching as installed
-    int32_t pad;
+    int32_t profile_cap; // phases recorded in `profile`
+    int32_t* profile;    // per phase: levels, endpoints, first and last level with an endpoint (nullable)
     long long wait_ns;   // limit of one barrier wait
     long long total_ns;  // limit of the whole launch
 };
@@ -202,7 +203,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, Smem& sm) {
 // one per thread).  Returns false (in every thread of the block) when the
 // wait ran out of time, the launch deadline passed or any block recorded an
 // error; the caller then leaves the kernel.
-__device__ __noinline__ bool grid_sync(Ctl* ctl, unsigned long long& target, long long wait_ns,
+static __device__ __noinline__ bool grid_sync(Ctl* ctl, unsigned long long& target, long long wait_ns,
                                        unsigned long long deadline, Smem& sm,
                                        const int32_t* a_ptr, const int32_t* b_ptr) {
     __syncthreads();
@@ -279,101 +280,123 @@ __device__ __forceinline__ void step_init(const Params& p, int slot, Counters& c
 // Expands the queue segment [qb, qe) whose columns are at level lvl
 // (Algorithm 2 / 4 loop body for every edge of every column).  New columns
 // are appended at qe + (slot count), endpoints at ebase + (slot count).
+// Loads tile entries [qb + first, qb + first + tw) of the queue (one per
+// thread; threads >= tw idle), applies the GPUBFS-WR root test, and lays the
+// tile's adjacency out in shared memory: sm.off (exclusive prefix of degrees),
+// sm.beg, sm.col, sm.root, sm.total.  If tile_ctr is given, thread 0 also
+// takes the next tile index from it (into sm.tile).  Ends with __syncthreads.
+template <bool WR>
+__device__ __forceinline__ void tile_load(const Params& p, int qb, int q, int first, int tw, Smem& sm,
+                                          Counters& cnt, int32_t* tile_ctr) {
+    const int t = threadIdx.x;
+    const int i = first + t;
+    int c = -1, beg = 0, deg = 0, myroot = -1;
+    if (t < tw && i < q) {
+        c = __ldcg(&p.queue[qb + i]);
+        if (WR) {
+            myroot = __ldcg(&p.root[c]);
+            if (__ldcg(&p.level[myroot]) < L0 - 1) c = -1;  // Algorithm 4: root already served
+        }
+        if (c >= 0) {
+            beg = __ldg(&p.col_ptr[c]);
+            deg = __ldg(&p.col_ptr[c + 1]) - beg;
+            cnt.cols++;
+        }
+    }
+    const int off = block_exclusive_scan(deg, sm);
+    sm.off[t] = off;
+    sm.beg[t] = beg;
+    sm.col[t] = c;
+    sm.root[t] = myroot;
+    if (t == 0 && tile_ctr) sm.tile = gridDim.x + atomicAdd(tile_ctr, 1);
+    __syncthreads();
+}
+
+// Visits every edge of the loaded tile (Algorithm 2 / 4 loop body), ILP edges
+// per thread with their loads in flight together.  push_col(cm) appends a
+// column inserted at level lvl + 1, push_end(r) an endpoint row.
+template <bool WR, class PushCol, class PushEnd>
+__device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, Smem& sm, Counters& cnt,
+                                           PushCol push_col, PushEnd push_end) {
+    const int T = blockDim.x;
+    const int t = threadIdx.x;
+    const int total = sm.total;
+    cnt.edges += (t == 0) ? total : 0;
+    for (int e0 = 0; e0 < total; e0 += T * ILP) {
+        int own[ILP], r[ILP], cm[ILP], lv[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            const int e = e0 + u * T + t;
+            own[u] = -1;
+            r[u] = -1;
+            if (e < total) {
+                int lo = 0, hi = tw - 1;  // last k with off[k] <= e
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (sm.off[mid] <= e) lo = mid; else hi = mid - 1;
+                }
+                own[u] = lo;
+                r[u] = __ldg(&p.row_idx[sm.beg[lo] + (e - sm.off[lo])]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) cm[u] = (own[u] >= 0) ? __ldcg(&p.rmatch[r[u]]) : -3;
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) lv[u] = (cm[u] >= 0) ? __ldcg(&p.level[cm[u]]) : 0;
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            if (own[u] < 0) continue;
+            const int col = sm.col[own[u]];
+            const int rt = sm.root[own[u]];
+            if (cm[u] >= 0) {
+                cnt.em++;
+                // matched row: its column joins the next level unless already reached
+                if (lv[u] == L0 - 1 && atomicCAS(&p.level[cm[u]], L0 - 1, lvl + 1) == L0 - 1) {
+                    __stcg(&p.pred[r[u]], col);
+                    if (WR) __stcg(&p.root[cm[u]], rt);
+                    push_col(cm[u]);
+                }
+            } else if (cm[u] == -1) {
+                // unmatched row: an augmenting path ends here
+                const int row = r[u];
+                if (WR && p.one_ep) {
+                    if (__ldcg(&p.level[rt]) == L0 && atomicCAS(&p.rmatch[row], -1, -2) == -1) {
+                        if (atomicCAS(&p.level[rt], L0, -row) == L0) {
+                            __stcg(&p.pred[row], col);
+                            push_end(row);
+                        } else {
+                            atomicExch(&p.rmatch[row], -1);  // root served meanwhile: give the row back
+                        }
+                    }
+                } else if (atomicCAS(&p.rmatch[row], -1, -2) == -1) {
+                    if (WR) __stcg(&p.level[rt], L0 - 2);
+                    __stcg(&p.pred[row], col);
+                    push_end(row);
+                }
+            }
+        }
+    }
+}
+
+// Expands the queue segment [qb, qe) whose columns are at level lvl, over the
+// whole grid.  New columns are appended at qe + (slot count), endpoints at
+// ebase + (slot count).
 template <bool WR>
 __device__ __forceinline__ void step_expand(const Params& p, int qb, int qe, int lvl, int slot,
                                             int ebase, Counters& cnt, Smem& sm) {
     const int q = qe - qb;
-    const int T = blockDim.x;
     // tile width: spread small frontiers over many blocks, never above blockDim
     int tw = (q + gridDim.x - 1) / gridDim.x;
     tw = (tw + 31) & ~31;
-    if (tw > T) tw = T;
+    if (tw > (int)blockDim.x) tw = blockDim.x;
     if (tw < 32) tw = 32;
     const int ntiles = (q + tw - 1) / tw;
-    int tile = blockIdx.x;
-    for (;;) {
-        if (tile >= ntiles) break;  // block-uniform
-        // ---- load the tile's columns: one per thread (threads >= tw idle here)
-        const int t = threadIdx.x;
-        const int i = tile * tw + t;
-        int c = -1, beg = 0, deg = 0, myroot = -1;
-        if (t < tw && i < q) {
-            c = __ldcg(&p.queue[qb + i]);
-            if (WR) {
-                myroot = __ldcg(&p.root[c]);
-                if (__ldcg(&p.level[myroot]) < L0 - 1) c = -1;  // Algorithm 4: root already served
-            }
-            if (c >= 0) {
-                beg = __ldg(&p.col_ptr[c]);
-                deg = __ldg(&p.col_ptr[c + 1]) - beg;
-                cnt.cols++;
-            }
-        }
-        const int off = block_exclusive_scan(deg, sm);
-        sm.off[t] = off;
-        sm.beg[t] = beg;
-        sm.col[t] = c;
-        sm.root[t] = myroot;
-        if (t == 0) sm.tile = gridDim.x + atomicAdd(&p.ctl->tcnt[slot], 1);
-        __syncthreads();
-        const int total = sm.total;
+    auto push_col = [&](int v) { push_block(p, sm, qe, slot, v); };
+    auto push_end = [&](int v) { push(p.endpoints, ebase, &p.ctl->ecnt[slot], v); };
+    for (int tile = blockIdx.x; tile < ntiles;) {  // block-uniform
+        tile_load<WR>(p, qb, q, tile * tw, tw, sm, cnt, &p.ctl->tcnt[slot]);
         const int next_tile = sm.tile;
-        cnt.edges += (t == 0) ? total : 0;
-        // ---- edges of the tile, ILP per thread
-        for (int e0 = 0; e0 < total; e0 += T * ILP) {
-            int own[ILP], r[ILP], cm[ILP], lv[ILP];
-#pragma unroll
-            for (int u = 0; u < ILP; ++u) {
-                const int e = e0 + u * T + t;
-                own[u] = -1;
-                r[u] = -1;
-                if (e < total) {
-                    int lo = 0, hi = tw - 1;  // last k with off[k] <= e
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (sm.off[mid] <= e) lo = mid; else hi = mid - 1;
-                    }
-                    own[u] = lo;
-                    r[u] = __ldg(&p.row_idx[sm.beg[lo] + (e - sm.off[lo])]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < ILP; ++u) cm[u] = (own[u] >= 0) ? __ldcg(&p.rmatch[r[u]]) : -3;
-#pragma unroll
-            for (int u = 0; u < ILP; ++u) lv[u] = (cm[u] >= 0) ? __ldcg(&p.level[cm[u]]) : 0;
-#pragma unroll
-            for (int u = 0; u < ILP; ++u) {
-                if (own[u] < 0) continue;
-                const int col = sm.col[own[u]];
-                const int rt = sm.root[own[u]];
-                if (cm[u] >= 0) {
-                    cnt.em++;
-                    // matched row: its column joins the next level unless already reached
-                    if (lv[u] == L0 - 1 && atomicCAS(&p.level[cm[u]], L0 - 1, lvl + 1) == L0 - 1) {
-                        __stcg(&p.pred[r[u]], col);
-                        if (WR) __stcg(&p.root[cm[u]], rt);
-                        push_block(p, sm, qe, slot, cm[u]);
-                    }
-                } else if (cm[u] == -1) {
-                    // unmatched row: an augmenting path ends here
-                    const int row = r[u];
-                    if (WR && p.one_ep) {
-                        if (__ldcg(&p.level[rt]) == L0 && atomicCAS(&p.rmatch[row], -1, -2) == -1) {
-                            if (atomicCAS(&p.level[rt], L0, -row) == L0) {
-                                __stcg(&p.pred[row], col);
-                                push(p.endpoints, ebase, &p.ctl->ecnt[slot], row);
-                            } else {
-                                atomicExch(&p.rmatch[row], -1);  // root served meanwhile: give the row back
-                            }
-                        }
-                    } else if (atomicCAS(&p.rmatch[row], -1, -2) == -1) {
-                        if (WR) __stcg(&p.level[rt], L0 - 2);
-                        __stcg(&p.pred[row], col);
-                        push(p.endpoints, ebase, &p.ctl->ecnt[slot], row);
-                    }
-                }
-            }
-        }
+        tile_edges<WR>(p, tw, lvl, sm, cnt, push_col, push_end);
         flush_block(p, sm, qe, slot);
         tile = next_tile;
     }

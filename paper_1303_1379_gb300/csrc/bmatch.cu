@@ -29,6 +29,7 @@ namespace {
 
 constexpr int kVersion = 1 * 10000 + 0 * 100 + 0;
 constexpr int kDefaultBlock = 512;
+constexpr int kProfileCap = 4096;
 
 // ------------------------------------------------------------------ kernels
 
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
         ++phases;
 
         // ---- BFS, level by level (Algorithm 1 inner loop)
-        int qb = 0, qe = n_roots, lvl = L0, n_ep = 0, levels = 0;
+        int qb = 0, qe = n_roots, lvl = L0, n_ep = 0, levels = 0, first_ep = 0, last_ep = 0;
         for (;;) {
             int s2 = step++;
             if (leader) { ctl->qcnt[(s2 + 1) % 3] = 0; ctl->ecnt[(s2 + 1) % 3] = 0; ctl->tcnt[(s2 + 1) % 3] = 0; }
@@ -77,6 +78,10 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
             const int nq = sm.bc_a;
             n_ep += sm.bc_b;
             ++levels;
+            if (sm.bc_b > 0) {
+                if (first_ep == 0) first_ep = levels;
+                last_ep = levels;
+            }
             ins_total += nq;
             if (nq == 0) break;                  // no vertex inserted
             if (p.mode == 1 && n_ep > 0) break;  // APsB: stop at the first level with a path
@@ -87,7 +92,16 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
         levels_total += levels;
         if (levels > levels_max) levels_max = levels;
         eps_total += n_ep;
-        if (leader) ctl->n_endpoints_last = n_ep;
+        if (leader) {
+            ctl->n_endpoints_last = n_ep;
+            if (p.profile && phases <= p.profile_cap) {
+                int32_t* pr = p.profile + 4 * (phases - 1);
+                pr[0] = levels;
+                pr[1] = n_ep;
+                pr[2] = first_ep;
+                pr[3] = last_ep;
+            }
+        }
 
         if (p.bfs_only) {
             step_release_endpoints(p, n_ep);
@@ -235,6 +249,7 @@ struct bm_ctx {
     int32_t* pred = nullptr;
     int32_t* queue = nullptr;
     int32_t* endpoints = nullptr;
+    int32_t* profile = nullptr;  // kProfileCap phases x 4
     Ctl* ctl = nullptr;
     Ctl* h_ctl = nullptr;  // pinned mirror
     int32_t sticky = 0;
@@ -321,6 +336,8 @@ Params make_params(bm_ctx* ctx, bool bfs_only) {
         p.phase_limit_is_error = 1;
     }
     p.bfs_only = bfs_only ? 1 : 0;
+    p.profile = ctx->profile;
+    p.profile_cap = kProfileCap;
     p.wait_ns = ctx->opt.wait_timeout_ns ? ctx->opt.wait_timeout_ns : 5000000000LL;
     p.total_ns = ctx->opt.total_timeout_ns ? ctx->opt.total_timeout_ns : 120000000000LL;
     return p;
@@ -374,7 +391,7 @@ int32_t run_host_loop(bm_ctx* ctx, const Params& p) {
         if (n_roots == 0) break;
         if (phases >= p.max_phases) { status = p.phase_limit_is_error ? BM_ERR_ITER_LIMIT : BM_INCOMPLETE; break; }
         ++phases;
-        int qb = 0, qe = n_roots, lvl = L0, n_ep = 0, levels = 0;
+        int qb = 0, qe = n_roots, lvl = L0, n_ep = 0, levels = 0, first_ep = 0, last_ep = 0;
         for (;;) {
             int s2 = step++;
             if ((rc = clear_slot(s2 % 3))) return rc;
@@ -385,6 +402,10 @@ int32_t run_host_loop(bm_ctx* ctx, const Params& p) {
             const int nq = h->qcnt[s2 % 3];
             n_ep += h->ecnt[s2 % 3];
             ++levels;
+            if (h->ecnt[s2 % 3] > 0) {
+                if (first_ep == 0) first_ep = levels;
+                last_ep = levels;
+            }
             ins_total += nq;
             if (nq == 0) break;
             if (p.mode == BM_APSB && n_ep > 0) break;
@@ -396,6 +417,11 @@ int32_t run_host_loop(bm_ctx* ctx, const Params& p) {
         levels_total += levels;
         if (levels > levels_max) levels_max = levels;
         eps_total += n_ep;
+        if (phases <= p.profile_cap) {
+            int32_t rec[4] = {levels, n_ep, first_ep, last_ep};
+            BM_CUDA(ctx, cudaMemcpyAsync(p.profile + 4 * (phases - 1), rec, sizeof(rec), cudaMemcpyHostToDevice, st));
+            BM_CUDA(ctx, cudaStreamSynchronize(st));
+        }
         if (p.bfs_only) {
             if (n_ep) k_release<<<grid_for(ctx, n_ep), blk, 0, st>>>(p, n_ep);
             BM_CUDA(ctx, cudaGetLastError());
@@ -540,7 +566,8 @@ int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* co
     size_t off_pd = off_rt + al(4 * nc1);
     size_t off_q = off_pd + al(4 * nr1);
     size_t off_ep = off_q + al(4 * nc1);
-    size_t off_cp = off_ep + al(4 * nr1);
+    size_t off_pf = off_ep + al(4 * nr1);
+    size_t off_cp = off_pf + al(4 * 4 * (size_t)kProfileCap);
     size_t total = off_cp;
     const bool own = (col_ptr == nullptr);
     size_t off_ri = 0;
@@ -568,6 +595,7 @@ int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* co
     ctx->pred = (int32_t*)(a + off_pd);
     ctx->queue = (int32_t*)(a + off_q);
     ctx->endpoints = (int32_t*)(a + off_ep);
+    ctx->profile = (int32_t*)(a + off_pf);
     if (own) {
         ctx->owns_csr = true;
         ctx->col_ptr = (int32_t*)(a + off_cp);
@@ -760,6 +788,33 @@ int32_t bm_bfs(bm_ctx* ctx, int32_t* level_out, int32_t* root_out, int32_t* pred
     if (n_endpoints_out) *n_endpoints_out = n_ep;
     rc = finish(ctx, nullptr, nullptr);
     return rc == BM_INCOMPLETE ? BM_OK : rc;
+}
+
+int32_t bm_phase_profile(bm_ctx* ctx, int32_t cap, int32_t* levels, int32_t* endpoints,
+                         int32_t* first_ep_level, int32_t* last_ep_level, int32_t* n_out) {
+    if (!ctx || cap < 0 || !n_out) return BM_ERR_INVALID_ARG;
+    if (ctx->sticky) return BM_ERR_STATE;
+    int32_t rc = sync_ctl(ctx);
+    if (rc) return rc;
+    int n = ctx->h_ctl->phases - 1;  // phases that searched with at least one root
+    if (n < 0) n = 0;
+    if (n > kProfileCap) n = kProfileCap;
+    if (n > cap) n = cap;
+    *n_out = n;
+    if (n == 0) return BM_OK;
+    int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)n);
+    if (!tmp) return BM_ERR_NOMEM;
+    cudaError_t e = cudaMemcpyAsync(tmp, ctx->profile, sizeof(int32_t) * 4 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) { free(tmp); return cuda_fail(ctx, e); }
+    for (int i = 0; i < n; ++i) {
+        if (levels) levels[i] = tmp[4 * i];
+        if (endpoints) endpoints[i] = tmp[4 * i + 1];
+        if (first_ep_level) first_ep_level[i] = tmp[4 * i + 2];
+        if (last_ep_level) last_ep_level[i] = tmp[4 * i + 3];
+    }
+    free(tmp);
+    return BM_OK;
 }
 
 int32_t bm_destroy(bm_ctx* ctx) {

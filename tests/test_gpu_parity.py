@@ -322,3 +322,20 @@ def test_full_size_workloads(name):
         cm = torch.empty(g.n_cols, dtype=torch.int32, device="cuda")
         res = m.match(rm, cm)
     assert_maximum(g, rm.cpu().numpy(), cm.cpu().numpy(), res.card, want)
+
+
+@pytest.mark.parametrize("driver", [0, 1])
+def test_phase_profile_matches_counters(c1, driver):
+    """The per-phase profile (Fig. 2's levels per outer iteration) adds up to
+    the launch counters, and every endpoint level lies inside its phase."""
+    cp, ri = to_dev(c1)
+    with bmatch.Matcher(c1.n_rows, c1.n_cols, c1.nnz, cp, ri, driver=driver) as m:
+        res = m.match()
+        levels, ends, first, last = m.phase_profile()
+    st = res.stats
+    assert len(levels) == st["phases"] - 1
+    assert int(levels.sum()) == st["levels"] and int(levels.max()) == st["max_levels_in_phase"]
+    assert int(ends.sum()) == st["endpoints"]
+    assert np.all((ends > 0) == (first > 0))
+    assert np.all(first <= last) and np.all(last <= levels)
+    assert ends[-1] == 0  # the last searching phase found no path
