@@ -136,7 +136,7 @@ BM_API const char *bm_status_string(int32_t status);
  *   stream: cudaStream_t to issue all work on (NULL = the legacy default stream).
  *   opt: NULL for defaults.
  * The context owns its workspace (matching, levels, roots, predecessors, one
- * column queue, the endpoint list: about 4*(3*n_cols + 3*n_rows) bytes),
+ * (column, root) queue, the endpoint list: about 4*(5*n_cols + 3*n_rows) bytes),
  * allocated here.  The matching starts empty.
  */
 BM_API int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *col_ptr,
@@ -295,6 +295,82 @@ BM_API int32_t bm_batch_autotune(bm_batch *b, int32_t greedy, const int32_t *rma
 /* Releases the batch's workspace (never the caller's buffers). */
 BM_API int32_t bm_batch_destroy(bm_batch *b);
 
+/* ------------------------------------------------------------------ serving
+ * Continuous-batching server (this library's addition around the paper's
+ * method).  Requests are host CSR graphs submitted at any time.  A scheduler
+ * thread admits them in arrival order when their device memory -- CSR,
+ * matching and workspace, about 4*(nnz + 6*n_cols + 3*n_rows) bytes -- fits in
+ * a fixed device pool and a ring slot is free, uploads them on a copy stream
+ * and publishes them to persistent worker blocks on the GPU, each of which
+ * matches one request at a time (cheap matching + Algorithm 1, the batched
+ * path's block routine) and reports |M| back through host-mapped memory.
+ * Requests that arrive while others run are taken by whichever worker frees
+ * first.  Workers leave after idle_timeout_ns without work and are relaunched
+ * when work arrives; every device-side wait is bounded.
+ */
+typedef struct bm_server_options {
+    int64_t pool_bytes;      /* device pool for resident requests; 0 = free memory - reserve     */
+    int64_t reserve_bytes;   /* left free when pool_bytes = 0 (default 2 GiB)                    */
+    int32_t ring_slots;      /* requests admitted at once (default 1024)                         */
+    int32_t block_size;      /* threads per worker block (default 512)                           */
+    int32_t blocks_per_sm;   /* worker blocks per SM (default 2, capped by occupancy)            */
+    int32_t mode;            /* BM_APFB (default) / BM_APSB                                      */
+    int32_t bfs;             /* BM_GPUBFS_WR (default) / BM_GPUBFS                               */
+    int32_t keep_results;    /* 1: keep each request's matching until bm_server_release          */
+    int64_t idle_timeout_ns; /* workers leave after this long without work (default 20 ms)       */
+    int32_t poll_interval_us;/* scheduler sleep when idle (default 5)                             */
+    int32_t reserved0;
+    int64_t reserved[4];
+} bm_server_options;
+
+/* Request states reported by bm_server_poll / bm_server_wait. */
+#define BM_REQ_PENDING 0
+#define BM_REQ_UPLOADING 1
+#define BM_REQ_RUNNING 2
+#define BM_REQ_DONE 3
+#define BM_REQ_CANCELLED 4
+
+typedef struct bm_request_info {
+    int32_t state;       /* BM_REQ_*                                                    */
+    int32_t status;      /* when done: BM_OK, BM_ERR_INVALID_CSR, BM_ERR_TOO_LARGE, ... */
+    int32_t card;        /* when done: |M|                                              */
+    int32_t phases;
+    int64_t latency_ns;  /* when done: submit -> completion seen by the scheduler     */
+    int64_t reserved[2];
+} bm_request_info;
+
+typedef struct bm_server_stats {
+    int64_t pending, inflight, completed, rejected, worker_launches, pool_bytes, pool_used;
+    int32_t grid, block;
+    int64_t reserved[2];
+} bm_server_stats;
+
+typedef struct bm_server bm_server;
+
+BM_API void bm_server_default_options(bm_server_options *opt);
+/* Allocates the pool and the host-mapped ring, starts the scheduler thread. */
+BM_API int32_t bm_server_create(const bm_server_options *opt, bm_server **out);
+/* Queues a request (host CSR, pinned preferred; the buffers must stay valid
+ * and unchanged until the request is done or cancelled).  *id_out gets its id.
+ * A request too large for the pool is completed at once with BM_ERR_TOO_LARGE;
+ * a malformed CSR completes with BM_ERR_INVALID_CSR (checked on the GPU). */
+BM_API int32_t bm_server_submit(bm_server *s, int32_t n_rows, int32_t n_cols, int64_t nnz,
+                                const int32_t *h_col_ptr, const int32_t *h_row_idx,
+                                int32_t greedy, int64_t *id_out);
+/* Non-blocking state of a request. */
+BM_API int32_t bm_server_poll(bm_server *s, int64_t id, bm_request_info *info);
+/* Waits up to timeout_ns for a request to finish (BM_ERR_TIMEOUT otherwise). */
+BM_API int32_t bm_server_wait(bm_server *s, int64_t id, int64_t timeout_ns, bm_request_info *info);
+/* Cancels a request that has not been admitted yet (else BM_ERR_STATE). */
+BM_API int32_t bm_server_cancel(bm_server *s, int64_t id);
+/* Copies a finished request's matching to host arrays (needs keep_results). */
+BM_API int32_t bm_server_fetch(bm_server *s, int64_t id, int32_t *h_rmatch, int32_t *h_cmatch);
+/* Forgets a finished or cancelled request and frees its pool memory. */
+BM_API int32_t bm_server_release(bm_server *s, int64_t id);
+BM_API int32_t bm_server_get_stats(bm_server *s, bm_server_stats *st);
+/* Stops the scheduler and the workers and frees everything. */
+BM_API int32_t bm_server_destroy(bm_server *s);
+
 /*
  * Allocation-free matching (no counterpart in the paper; an addition for
  * callers that may not allocate).
@@ -314,7 +390,7 @@ BM_API int32_t bm_batch_destroy(bm_batch *b);
  *                     return.  Caller-owned.
  *   stream            cudaStream_t for all work (NULL = legacy default stream).
  *   card_out          host, nullable: |M|.
- * Size limit: 512 + 4*(3*n_cols + 2*n_rows) bytes (each array rounded up to
+ * Size limit: 512 + 4*(4*n_cols + 2*n_rows) bytes (each array rounded up to
  * 256 bytes) must fit in BM_NOALLOC_SCRATCH_BYTES, else BM_ERR_TOO_LARGE is
  * returned before any GPU work.  Invalid CSR or matching: BM_ERR_INVALID_CSR /
  * BM_ERR_INVALID_MATCHING (rmatch/cmatch unchanged then).

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libbmatch.so")
-SOURCES = [os.path.join(CSRC, f) for f in ("bmatch.cu", "bm_batch.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("bmatch.cu", "bm_batch.cu", "bm_server.cu")]
 DEPENDS = SOURCES + [os.path.join(CSRC, "bm_device.cuh"), os.path.join(INCLUDE, "bmatch.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -53,7 +53,7 @@ struct BatchParams {
     int32_t* level;
     int32_t* root;
     int32_t* pred;
-    int32_t* queue;
+    int2* queue;
     int32_t* endpoints;
     int32_t* card_out;    // [n_graphs]
     int32_t* status_out;  // [n_graphs]
@@ -61,133 +61,13 @@ struct BatchParams {
     BatchCtl* ctl;
 };
 
-__device__ __forceinline__ void block_count_add(long long& acc, long long v) { acc += v; }
-
-// One graph, one block.  Returns the graph's status.
 template <bool WR>
-__device__ int block_match(const BatchParams& bp, const Params& p, Smem& sm, Counters& cnt, int& card_out,
-                           int& phases_out, long long& levels_out, long long& eps_out) {
-    const int T = blockDim.x;
-    const int t = threadIdx.x;
-    const int nr = p.nr, nc = p.nc;
-    // ---- cheap matching (Section 4): unmatched columns claim their first free row
-    if (bp.greedy) {
-        for (int c = t; c < nc; c += T) {
-            if (p.cmatch[c] != -1) continue;
-            const int end = __ldg(&p.col_ptr[c + 1]);
-            for (int e = __ldg(&p.col_ptr[c]); e < end; ++e) {
-                const int r = __ldg(&p.row_idx[e]);
-                if (bmd::ld_volatile(&p.rmatch[r]) == -1 && atomicCAS(&p.rmatch[r], -1, c) == -1) {
-                    p.cmatch[c] = r;
-                    break;
-                }
-            }
-        }
-        __syncthreads();
-    }
-    const int max_phases = (nr < nc ? nr : nc) + 2;
-    int phases = 0, card = 0, status = 0;
-    long long levels_total = 0, eps_total = 0;
-    for (;;) {
-        // ---- InitBfsArray (+ column half of FixMatching)
-        if (t == 0) { sm.qn = 0; sm.qbase = 0; sm.total = 0; }
-        __syncthreads();
-        int nfree = 0;
-        for (int c = t; c < nc; c += T) {
-            int r = __ldcg(&p.cmatch[c]);
-            if (r >= 0 && __ldcg(&p.rmatch[r]) != c) {
-                __stcg(&p.cmatch[c], -1);
-                r = -1;
-                cnt.fixes++;
-            }
-            const bool is_free = r < 0;
-            __stcg(&p.level[c], is_free ? L0 : L0 - 1);
-            if (WR) __stcg(&p.root[c], is_free ? c : -1);
-            if (is_free) {
-                ++nfree;
-                if (__ldg(&p.col_ptr[c + 1]) > __ldg(&p.col_ptr[c])) p.queue[atomicAdd(&sm.qn, 1)] = c;
-            }
-        }
-#pragma unroll
-        for (int s = 16; s >= 1; s >>= 1) nfree += __shfl_down_sync(bmd::FULL, nfree, s);
-        if ((t & 31) == 0 && nfree) atomicAdd(&sm.total, nfree);
-        __syncthreads();
-        const int n_roots = sm.qn;
-        card = nc - sm.total;
-        if (n_roots == 0) break;
-        if (phases >= max_phases) { status = BM_ERR_ITER_LIMIT; break; }
-        ++phases;
-        // ---- BFS levels; sm.qn is the queue tail, sm.qbase the endpoint count
-        int qb = 0, qe = n_roots, lvl = L0, levels = 0, n_ep = 0;
-        auto push_col = [&](int v) { p.queue[atomicAdd(&sm.qn, 1)] = v; };
-        auto push_end = [&](int v) { p.endpoints[atomicAdd(&sm.qbase, 1)] = v; };
-        for (;;) {
-            const int q = qe - qb;
-            for (int first = 0; first < q; first += T) {
-                bmd::tile_load<WR>(p, qb, q, first, T, sm, cnt, nullptr);
-                bmd::tile_edges<WR>(p, T, lvl, sm, cnt, push_col, push_end);
-                __syncthreads();  // sm.off/beg/col/root are reused by the next tile
-            }
-            __syncthreads();
-            const int tail = sm.qn;
-            const int eps = sm.qbase;
-            ++levels;
-            if (tail == qe) { n_ep = eps; break; }  // no vertex inserted
-            if (bp.mode == BM_APSB && eps > 0) { n_ep = eps; break; }
-            if (levels > nc + 2) { status = BM_ERR_ITER_LIMIT; n_ep = eps; break; }
-            qb = qe;
-            qe = tail;
-            ++lvl;
-        }
-        levels_total += levels;
-        eps_total += n_ep;
-        if (status) break;
-        if (n_ep == 0) break;  // no augmenting path: maximum (Berge)
-        // ---- Alternate (Algorithm 3) and the row half of FixMatching
-        for (int i = t; i < n_ep; i += T) {
-            int r = __ldcg(&p.endpoints[i]);
-            int steps = 0;
-            while (r != -1) {
-                if (++steps > levels + 2) { atomicCAS(&sm.ok, 0, BM_ERR_ITER_LIMIT); break; }
-                const int c = __ldcg(&p.pred[r]);
-                if ((unsigned)c >= (unsigned)nc) { atomicCAS(&sm.ok, 0, BM_ERR_STATE); break; }
-                const int r2 = bmd::ld_volatile(&p.cmatch[c]);
-                if (r2 >= 0 && __ldcg(&p.pred[r2]) == c) break;
-                bmd::st_volatile(&p.cmatch[c], r);
-                __stcg(&p.rmatch[r], c);
-                cnt.alt++;
-                r = r2;
-            }
-        }
-        __syncthreads();
-        for (int r = t; r < nr; r += T) {
-            const int m = __ldcg(&p.rmatch[r]);
-            if (m == -1) continue;
-            if (m < 0 || __ldcg(&p.cmatch[m]) != r) {
-                __stcg(&p.rmatch[r], -1);
-                cnt.fixes++;
-            }
-        }
-        __syncthreads();
-        if (sm.ok != 0) { status = sm.ok; break; }
-    }
-    card_out = card;
-    phases_out = phases + 1;
-    levels_out = levels_total;
-    eps_out = eps_total;
-    return status;
-}
-
-template <bool WR>
-__global__ void __launch_bounds__(1024) k_batch(BatchParams bp) {
+__global__ void __launch_bounds__(1024, 1) k_batch(BatchParams bp) {
     __shared__ Smem sm;
     Counters cnt{0, 0, 0, 0, 0};
     long long lv_all = 0, ep_all = 0, ph_all = 0;
     for (;;) {
-        if (threadIdx.x == 0) {
-            sm.tile = atomicAdd(&bp.ctl->next, 1);
-            sm.ok = 0;
-        }
+        if (threadIdx.x == 0) sm.tile = atomicAdd(&bp.ctl->next, 1);
         __syncthreads();
         const int pos = sm.tile;
         if (pos >= bp.n_graphs) break;
@@ -209,7 +89,7 @@ __global__ void __launch_bounds__(1024) k_batch(BatchParams bp) {
         p.one_ep = bp.one_ep;
         int card = 0, phases = 0;
         long long levels = 0, eps = 0;
-        const int st = block_match<WR>(bp, p, sm, cnt, card, phases, levels, eps);
+        const int st = bmd::block_match_graph<WR, true>(p, bp.greedy, sm, cnt, card, phases, levels, eps);
         if (threadIdx.x == 0) {
             bp.card_out[g] = card;
             bp.status_out[g] = st;
@@ -278,8 +158,9 @@ struct bm_batch {
     bm_options opt{};
     int block = 512, grid = 0, num_sms = 0;
     void* arena = nullptr;
-    int32_t *order = nullptr, *level = nullptr, *root = nullptr, *pred = nullptr, *queue = nullptr,
-            *endpoints = nullptr, *card = nullptr, *status = nullptr, *phases = nullptr;
+    int32_t *order = nullptr, *level = nullptr, *root = nullptr, *pred = nullptr, *endpoints = nullptr,
+            *card = nullptr, *status = nullptr, *phases = nullptr;
+    int2* queue = nullptr;
     BatchCtl* ctl = nullptr;
     BatchCtl* h_ctl = nullptr;
     cudaGraph_t graph = nullptr;
@@ -436,7 +317,7 @@ int32_t bm_batch_create(const bm_batch_desc* desc, void* stream, const bm_option
     const size_t o_ph = off; off += al(4 * G1);
     const size_t o_lv = off; off += al(4 * C);
     const size_t o_rt = off; off += al(4 * C);
-    const size_t o_q = off; off += al(4 * C);
+    const size_t o_q = off; off += al(8 * C);
     const size_t o_pd = off; off += al(4 * R);
     const size_t o_ep = off; off += al(4 * R);
     if (cudaMalloc(&b->arena, off) != cudaSuccess || cudaMallocHost((void**)&b->h_ctl, sizeof(BatchCtl)) != cudaSuccess) {
@@ -452,7 +333,7 @@ int32_t bm_batch_create(const bm_batch_desc* desc, void* stream, const bm_option
     b->phases = (int32_t*)(a + o_ph);
     b->level = (int32_t*)(a + o_lv);
     b->root = (int32_t*)(a + o_rt);
-    b->queue = (int32_t*)(a + o_q);
+    b->queue = (int2*)(a + o_q);
     b->pred = (int32_t*)(a + o_pd);
     b->endpoints = (int32_t*)(a + o_ep);
     int32_t rc = configure_batch(b);

@@ -40,7 +40,7 @@ namespace cg = cooperative_groups;
 constexpr int L0 = 2;  // BFS start level (Section 3 chooses L0 = 2)
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int MAX_BLOCK = 1024;
-constexpr int QBUF = 4096;  // per-block append buffer (entries)
+constexpr int QBUF = 2048;  // per-block append buffer (entries)
 constexpr int ILP = 4;      // edges per thread in flight
 
 // Control block in device memory, cleared before every launch.  Per-step
@@ -48,20 +48,23 @@ constexpr int ILP = 4;      // edges per thread in flight
 // slot (s + 1) % 3, which nobody reads during step s (it was last read right
 // after the barrier that ended step s - 2).
 struct alignas(128) Ctl {
-    unsigned long long bar;    // grid barrier arrivals (monotone)
-    int32_t pad_bar[30];
-    unsigned long long epoch;  // grid barrier releases (monotone)
-    int32_t pad_epoch[30];
-    int32_t qcnt[3];           // columns appended during a step
-    int32_t ecnt[3];           // endpoints appended during a step (init: free columns)
+    // grid barrier: arrival words rotate over barriers b % 3; each arrival adds
+    // 1 + (block has endpoints) << 11 + (block's appended columns) << 22
+    unsigned long long arrive[3][16];
+    // release word: (barrier id + 1) << 43 | blocks with endpoints << 32 | appended columns
+    unsigned long long release;
+    int32_t pad_rel[30];
+    int32_t qcnt[3];           // columns appended during a step (queue positions)
+    int32_t ecnt[3];           // init: unmatched columns counted during a step
     int32_t tcnt[3];           // tiles handed out during a step
+    int32_t ep_phase;          // endpoints appended in the current phase (positions)
     int32_t err;               // first error code (0 = none)
     int32_t status;            // final status of the launch
     int32_t card;              // |M| at the end
     int32_t initial_card;
     int32_t phases;
     int32_t n_endpoints_last;  // endpoints of the last BFS (inspection)
-    int32_t pad1[15];
+    int32_t pad1[14];
     long long levels;
     long long max_levels;
     long long cols_expanded;
@@ -83,7 +86,7 @@ struct Params {
     int32_t* level;      // bfs_array of the paper
     int32_t* root;       // root array of GPUBFS-WR
     int32_t* pred;       // predecessor array
-    int32_t* queue;      // columns of the current phase, level by level
+    int2* queue;         // (column, root) of the current phase, level by level
     int32_t* endpoints;  // rows claimed as path ends in the current phase
     Ctl* ctl;
     int32_t mode;        // 0 APFB, 1 APsB
@@ -100,16 +103,18 @@ struct Params {
 // Per-block shared state of the steps.
 struct Smem {
     int tile;
-    int qn;     // entries in qbuf (may exceed QBUF: the excess went straight to global memory)
+    int qn;     // appends since the last flush (may exceed QBUF: the excess went to global memory)
     int qbase;  // global position of the flushed buffer
     int total;  // edges of the current tile
-    int bc_a, bc_b, ok;  // barrier broadcast
+    int npush;  // columns this block appended during the current step
+    int has_ep; // this block appended an endpoint during the current step
+    int bc_a, bc_b, bc_c, ok;  // barrier broadcast
     int wsum[32];
     int off[MAX_BLOCK];  // exclusive prefix of the tile's degrees
     int beg[MAX_BLOCK];  // first edge of each tile column
-    int col[MAX_BLOCK];
+    int col[MAX_BLOCK];  // column, or -1 if its root is already served
     int root[MAX_BLOCK];
-    int qbuf[QBUF];
+    int2 qbuf[QBUF];
 };
 
 // ------------------------------------------------------------------ memory helpers
@@ -137,9 +142,18 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 
 __device__ __forceinline__ void set_error(Ctl* ctl, int code) { atomicCAS(&ctl->err, 0, code); }
 
+// CSR reads: through the read-only (non-coherent) path when the CSR cannot
+// change during the kernel (NC), else through L2 only.
+template <bool NC>
+__device__ __forceinline__ int ld_csr(const int32_t* p) {
+    if (NC) return __ldg(p);
+    return __ldcg(p);
+}
+
 // Appends v at base + (running count of `slot`) with one atomic per group of
-// converged lanes (used for the rare endpoint appends and buffer overflow).
-__device__ __forceinline__ void push(int32_t* buf, int base, int32_t* slot, int v) {
+// converged lanes (endpoints, and columns when the block buffer is full).
+template <class T>
+__device__ __forceinline__ void push(T* buf, int base, int32_t* slot, T v) {
     cg::coalesced_group g = cg::coalesced_threads();
     int pos = 0;
     if (g.thread_rank() == 0) pos = atomicAdd(slot, (int)g.size());
@@ -147,19 +161,22 @@ __device__ __forceinline__ void push(int32_t* buf, int base, int32_t* slot, int 
     buf[base + pos] = v;
 }
 
-// Appends a column to the block's buffer (global fallback when it is full).
-__device__ __forceinline__ void push_block(const Params& p, Smem& sm, int qbase, int slot, int v) {
+// Appends a (column, root) entry to the block's buffer (global fallback when it is full).
+__device__ __forceinline__ void push_block(const Params& p, Smem& sm, int qbase, int slot, int2 v) {
     const int pos = atomicAdd(&sm.qn, 1);
     if (pos < QBUF) sm.qbuf[pos] = v;
     else push(p.queue, qbase, &p.ctl->qcnt[slot], v);
 }
 
-// Writes the block's buffer to queue[qbase + ...] with one global atomic.
-// Called by all threads of the block.
+// Writes the block's buffer to queue[qbase + ...] with one global atomic and
+// adds this tile's appends to sm.npush.  Called by all threads of the block.
 __device__ __forceinline__ void flush_block(const Params& p, Smem& sm, int qbase, int slot) {
     __syncthreads();
     const int n = min(sm.qn, QBUF);
-    if (n > 0 && threadIdx.x == 0) sm.qbase = atomicAdd(&p.ctl->qcnt[slot], n);
+    if (threadIdx.x == 0) {
+        sm.npush += sm.qn;
+        if (n > 0) sm.qbase = atomicAdd(&p.ctl->qcnt[slot], n);
+    }
     __syncthreads();
     if (n > 0) {
         const int b = qbase + sm.qbase;
@@ -195,41 +212,68 @@ __device__ __forceinline__ int block_exclusive_scan(int v, Smem& sm) {
     return (warp > 0 ? sm.wsum[warp - 1] : 0) + incl - v;
 }
 
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_u64(unsigned long long* p, unsigned long long v) {
+    unsigned long long r;
+    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(v) : "memory");
+    return r;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 // ------------------------------------------------------------------ grid barrier
-// All blocks of a cooperative launch.  Arrivals count up one word; the last
-// arriver publishes the new epoch on another word, which the others poll.
-// If a_ptr/b_ptr are given, thread 0 reads them after the barrier and the
-// values are returned through sm.bc_a / sm.bc_b (one read per block instead of
-// one per thread).  Returns false (in every thread of the block) when the
-// wait ran out of time, the launch deadline passed or any block recorded an
-// error; the caller then leaves the kernel.
-static __device__ __noinline__ bool grid_sync(Ctl* ctl, unsigned long long& target, long long wait_ns,
-                                       unsigned long long deadline, Smem& sm,
-                                       const int32_t* a_ptr, const int32_t* b_ptr) {
+// All blocks of a cooperative launch.  Block b of the grid adds one arrival,
+// a flag (sm.has_ep) and its appended-column count (sm.npush) to the arrival
+// word of this barrier with one acquire-release atomic; the last arriver
+// publishes the sums with the barrier id in one release store, which the
+// others poll with relaxed loads (one acquire fence after the wait).  So
+// every block learns the level's totals without reading a counter after the
+// barrier: sm.bc_a = appended columns, sm.bc_b = blocks that found endpoints.
+// If extra_ptr is given, thread 0 also reads it after the barrier into
+// sm.bc_c.  Returns false (in every thread of the block) when the wait ran
+// out of time, the launch deadline passed or a block recorded an error; the
+// caller then leaves the kernel.
+static __device__ __noinline__ bool grid_sync(Ctl* ctl, int& bid, long long wait_ns,
+                                              unsigned long long deadline, Smem& sm,
+                                              const int32_t* extra_ptr) {
     __syncthreads();
-    target += gridDim.x;
+    const int b = bid++;
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
-        const unsigned long long prev = atomicAdd(&ctl->bar, 1ull);
-        if (prev + 1 == target) {
-            __threadfence();
-            st_release_u64(&ctl->epoch, target);
+        const unsigned long long inc =
+            1ull + ((unsigned long long)(sm.has_ep ? 1 : 0) << 11) + ((unsigned long long)sm.npush << 22);
+        const unsigned long long prev = atom_add_acq_rel_u64(&ctl->arrive[b % 3][0], inc);
+        const unsigned long long want = (unsigned long long)((b + 1) & 0x1FFFFF);
+        unsigned long long rel;
+        if ((prev & 0x7FFull) + 1 == gridDim.x) {
+            const unsigned long long tot = prev + inc;
+            st_relaxed_u64(&ctl->arrive[(b + 2) % 3][0], 0ull);  // barrier b + 2's word, idle since b - 1
+            rel = (want << 43) | (((tot >> 11) & 0x7FFull) << 32) | ((tot >> 22) & 0xFFFFFFFFull);
+            st_release_u64(&ctl->release, rel);
         } else {
             unsigned long long t_end = globaltimer() + (unsigned long long)wait_ns;
             if (t_end > deadline) t_end = deadline;
             unsigned spins = 0;
-            while (ld_acquire_u64(&ctl->epoch) < target) {
+            for (;;) {
+                rel = ld_relaxed_u64(&ctl->release);
+                if ((rel >> 43) == want) break;
                 if ((++spins & 15u) == 0) {
                     if (ld_volatile(&ctl->err) != 0) { ok = 0; break; }
                     if (globaltimer() > t_end) { set_error(ctl, -5 /*BM_ERR_TIMEOUT*/); ok = 0; break; }
                 }
             }
-            __threadfence();
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
         }
-        if (ok && ld_volatile(&ctl->err) != 0) ok = 0;
-        if (a_ptr) sm.bc_a = ld_volatile(a_ptr);
-        if (b_ptr) sm.bc_b = ld_volatile(b_ptr);
+        sm.bc_a = (int)(rel & 0xFFFFFFFFull);
+        sm.bc_b = (int)((rel >> 32) & 0x7FFull);
+        if (extra_ptr) sm.bc_c = ld_volatile(extra_ptr);
+        sm.npush = 0;
+        sm.has_ep = 0;
         sm.ok = ok;
     }
     __syncthreads();
@@ -266,7 +310,7 @@ __device__ __forceinline__ void step_init(const Params& p, int slot, Counters& c
             if (WR) __stcg(&p.root[c], is_free ? c : -1);
             if (is_free) {
                 ++nfree;
-                if (__ldg(&p.col_ptr[c + 1]) > __ldg(&p.col_ptr[c])) push_block(p, sm, 0, slot, c);
+                if (__ldg(&p.col_ptr[c + 1]) > __ldg(&p.col_ptr[c])) push_block(p, sm, 0, slot, make_int2(c, c));
             }
         }
         flush_block(p, sm, 0, slot);
@@ -277,51 +321,51 @@ __device__ __forceinline__ void step_init(const Params& p, int slot, Counters& c
 }
 
 // ------------------------------------------------------------------ BFS level
-// Expands the queue segment [qb, qe) whose columns are at level lvl
-// (Algorithm 2 / 4 loop body for every edge of every column).  New columns
-// are appended at qe + (slot count), endpoints at ebase + (slot count).
 // Loads tile entries [qb + first, qb + first + tw) of the queue (one per
-// thread; threads >= tw idle), applies the GPUBFS-WR root test, and lays the
-// tile's adjacency out in shared memory: sm.off (exclusive prefix of degrees),
-// sm.beg, sm.col, sm.root, sm.total.  If tile_ctr is given, thread 0 also
+// thread; threads >= tw idle) and lays the tile's adjacency out in shared
+// memory: sm.off (exclusive prefix of degrees), sm.beg, sm.col, sm.root,
+// sm.total.  The queue entry carries the root, so the column's row range and
+// the GPUBFS-WR root test (Algorithm 4: skip the column if its root is already
+// served) are two independent loads whose latency overlaps the prefix sum; a
+// column whose root is served keeps its place in the prefix sum but gets
+// sm.col = -1 and its edges are skipped.  If tile_ctr is given, thread 0 also
 // takes the next tile index from it (into sm.tile).  Ends with __syncthreads.
-template <bool WR>
+template <bool WR, bool NC = true>
 __device__ __forceinline__ void tile_load(const Params& p, int qb, int q, int first, int tw, Smem& sm,
                                           Counters& cnt, int32_t* tile_ctr) {
     const int t = threadIdx.x;
     const int i = first + t;
-    int c = -1, beg = 0, deg = 0, myroot = -1;
+    int c = -1, beg = 0, deg = 0, myroot = -1, rlev = L0;
     if (t < tw && i < q) {
-        c = __ldcg(&p.queue[qb + i]);
-        if (WR) {
-            myroot = __ldcg(&p.root[c]);
-            if (__ldcg(&p.level[myroot]) < L0 - 1) c = -1;  // Algorithm 4: root already served
-        }
-        if (c >= 0) {
-            beg = __ldg(&p.col_ptr[c]);
-            deg = __ldg(&p.col_ptr[c + 1]) - beg;
-            cnt.cols++;
-        }
+        const int2 ent = __ldcg(&p.queue[qb + i]);
+        c = ent.x;
+        myroot = ent.y;
+        beg = ld_csr<NC>(&p.col_ptr[c]);
+        deg = ld_csr<NC>(&p.col_ptr[c + 1]) - beg;
+        if (WR) rlev = __ldcg(&p.level[myroot]);
     }
+    if (t == 0 && tile_ctr) sm.tile = gridDim.x + atomicAdd(tile_ctr, 1);
     const int off = block_exclusive_scan(deg, sm);
+    if (WR && rlev < L0 - 1) c = -1;  // Algorithm 4: root already served
+    if (c >= 0) cnt.cols++;
     sm.off[t] = off;
     sm.beg[t] = beg;
     sm.col[t] = c;
     sm.root[t] = myroot;
-    if (t == 0 && tile_ctr) sm.tile = gridDim.x + atomicAdd(tile_ctr, 1);
     __syncthreads();
 }
 
 // Visits every edge of the loaded tile (Algorithm 2 / 4 loop body), ILP edges
 // per thread with their loads in flight together.  push_col(cm) appends a
 // column inserted at level lvl + 1, push_end(r) an endpoint row.
-template <bool WR, class PushCol, class PushEnd>
-__device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, Smem& sm, Counters& cnt,
-                                           PushCol push_col, PushEnd push_end) {
+// direct: claim with the CAS alone (small frontiers: saves a dependent load);
+// otherwise test the level first and CAS only unvisited columns.
+template <bool WR, class PushCol, class PushEnd, bool NC = true>
+__device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, bool direct, Smem& sm,
+                                           Counters& cnt, PushCol push_col, PushEnd push_end) {
     const int T = blockDim.x;
     const int t = threadIdx.x;
     const int total = sm.total;
-    cnt.edges += (t == 0) ? total : 0;
     for (int e0 = 0; e0 < total; e0 += T * ILP) {
         int own[ILP], r[ILP], cm[ILP], lv[ILP];
 #pragma unroll
@@ -335,26 +379,29 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, Sme
                     const int mid = (lo + hi + 1) >> 1;
                     if (sm.off[mid] <= e) lo = mid; else hi = mid - 1;
                 }
-                own[u] = lo;
-                r[u] = __ldg(&p.row_idx[sm.beg[lo] + (e - sm.off[lo])]);
+                if (sm.col[lo] >= 0) {
+                    own[u] = lo;
+                    r[u] = ld_csr<NC>(&p.row_idx[sm.beg[lo] + (e - sm.off[lo])]);
+                }
             }
         }
 #pragma unroll
         for (int u = 0; u < ILP; ++u) cm[u] = (own[u] >= 0) ? __ldcg(&p.rmatch[r[u]]) : -3;
 #pragma unroll
-        for (int u = 0; u < ILP; ++u) lv[u] = (cm[u] >= 0) ? __ldcg(&p.level[cm[u]]) : 0;
+        for (int u = 0; u < ILP; ++u) lv[u] = (cm[u] >= 0 && !direct) ? __ldcg(&p.level[cm[u]]) : L0 - 1;
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
             if (own[u] < 0) continue;
             const int col = sm.col[own[u]];
             const int rt = sm.root[own[u]];
+            cnt.edges++;
             if (cm[u] >= 0) {
                 cnt.em++;
                 // matched row: its column joins the next level unless already reached
                 if (lv[u] == L0 - 1 && atomicCAS(&p.level[cm[u]], L0 - 1, lvl + 1) == L0 - 1) {
                     __stcg(&p.pred[r[u]], col);
                     if (WR) __stcg(&p.root[cm[u]], rt);
-                    push_col(cm[u]);
+                    push_col(make_int2(cm[u], rt));
                 }
             } else if (cm[u] == -1) {
                 // unmatched row: an augmenting path ends here
@@ -364,6 +411,7 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, Sme
                         if (atomicCAS(&p.level[rt], L0, -row) == L0) {
                             __stcg(&p.pred[row], col);
                             push_end(row);
+                            sm.has_ep = 1;
                         } else {
                             atomicExch(&p.rmatch[row], -1);  // root served meanwhile: give the row back
                         }
@@ -372,6 +420,7 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, Sme
                     if (WR) __stcg(&p.level[rt], L0 - 2);
                     __stcg(&p.pred[row], col);
                     push_end(row);
+                    sm.has_ep = 1;
                 }
             }
         }
@@ -380,10 +429,12 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, Sme
 
 // Expands the queue segment [qb, qe) whose columns are at level lvl, over the
 // whole grid.  New columns are appended at qe + (slot count), endpoints at
-// ebase + (slot count).
+// ep_phase (the phase's running count).  Frontiers of at most one tile per
+// block (the deep, narrow levels of long augmenting paths) take their tile
+// from blockIdx.x alone and claim columns by CAS without a test load.
 template <bool WR>
 __device__ __forceinline__ void step_expand(const Params& p, int qb, int qe, int lvl, int slot,
-                                            int ebase, Counters& cnt, Smem& sm) {
+                                            Counters& cnt, Smem& sm) {
     const int q = qe - qb;
     // tile width: spread small frontiers over many blocks, never above blockDim
     int tw = (q + gridDim.x - 1) / gridDim.x;
@@ -391,12 +442,13 @@ __device__ __forceinline__ void step_expand(const Params& p, int qb, int qe, int
     if (tw > (int)blockDim.x) tw = blockDim.x;
     if (tw < 32) tw = 32;
     const int ntiles = (q + tw - 1) / tw;
-    auto push_col = [&](int v) { push_block(p, sm, qe, slot, v); };
-    auto push_end = [&](int v) { push(p.endpoints, ebase, &p.ctl->ecnt[slot], v); };
+    const bool narrow = ntiles <= (int)gridDim.x;
+    auto push_col = [&](int2 v) { push_block(p, sm, qe, slot, v); };
+    auto push_end = [&](int v) { push(p.endpoints, 0, &p.ctl->ep_phase, v); };
     for (int tile = blockIdx.x; tile < ntiles;) {  // block-uniform
-        tile_load<WR>(p, qb, q, tile * tw, tw, sm, cnt, &p.ctl->tcnt[slot]);
-        const int next_tile = sm.tile;
-        tile_edges<WR>(p, tw, lvl, sm, cnt, push_col, push_end);
+        tile_load<WR>(p, qb, q, tile * tw, tw, sm, cnt, narrow ? nullptr : &p.ctl->tcnt[slot]);
+        const int next_tile = narrow ? ntiles : sm.tile;
+        tile_edges<WR>(p, tw, lvl, narrow, sm, cnt, push_col, push_end);
         flush_block(p, sm, qe, slot);
         tile = next_tile;
     }
@@ -450,6 +502,157 @@ __device__ __forceinline__ void step_release_endpoints(const Params& p, int n_ep
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthr = gridDim.x * blockDim.x;
     for (int i = tid; i < n_ep; i += nthr) __stcg(&p.rmatch[__ldcg(&p.endpoints[i])], -1);
+}
+
+// ------------------------------------------------------------------ one graph, one block
+// The whole method on one graph by one block (batched and served paths):
+// optional cheap matching, then Algorithm 1 with the steps separated by
+// __syncthreads; queue tail, endpoint count and free-column count live in
+// shared memory (sm.qn, sm.qbase, sm.total).  Returns the graph's status.
+template <bool WR, bool NC>
+__device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters& cnt, int& card_out,
+                                 int& phases_out, long long& levels_out, long long& eps_out) {
+    const int T = blockDim.x;
+    const int t = threadIdx.x;
+    const int nr = p.nr, nc = p.nc;
+    if (t == 0) sm.ok = 0;
+    // ---- cheap matching (Section 4): unmatched columns claim their first free row
+    if (greedy) {
+        for (int c = t; c < nc; c += T) {
+            if (__ldcg(&p.cmatch[c]) != -1) continue;
+            const int end = ld_csr<NC>(&p.col_ptr[c + 1]);
+            for (int e = ld_csr<NC>(&p.col_ptr[c]); e < end; ++e) {
+                const int r = ld_csr<NC>(&p.row_idx[e]);
+                if (ld_volatile(&p.rmatch[r]) == -1 && atomicCAS(&p.rmatch[r], -1, c) == -1) {
+                    p.cmatch[c] = r;
+                    break;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int max_phases = (nr < nc ? nr : nc) + 2;
+    int phases = 0, card = 0, status = 0;
+    long long levels_total = 0, eps_total = 0;
+    for (;;) {
+        // ---- InitBfsArray (+ column half of FixMatching)
+        if (t == 0) { sm.qn = 0; sm.qbase = 0; sm.total = 0; }
+        __syncthreads();
+        int nfree = 0;
+        for (int c = t; c < nc; c += T) {
+            int r = __ldcg(&p.cmatch[c]);
+            if (r >= 0 && __ldcg(&p.rmatch[r]) != c) {
+                __stcg(&p.cmatch[c], -1);
+                r = -1;
+                cnt.fixes++;
+            }
+            const bool is_free = r < 0;
+            __stcg(&p.level[c], is_free ? L0 : L0 - 1);
+            if (WR) __stcg(&p.root[c], is_free ? c : -1);
+            if (is_free) {
+                ++nfree;
+                if (ld_csr<NC>(&p.col_ptr[c + 1]) > ld_csr<NC>(&p.col_ptr[c]))
+                    p.queue[atomicAdd(&sm.qn, 1)] = make_int2(c, c);
+            }
+        }
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) nfree += __shfl_down_sync(FULL, nfree, s);
+        if ((t & 31) == 0 && nfree) atomicAdd(&sm.total, nfree);
+        __syncthreads();
+        const int n_roots = sm.qn;
+        card = nc - sm.total;
+        if (n_roots == 0) break;
+        if (phases >= max_phases) { status = -4 /*BM_ERR_ITER_LIMIT*/; break; }
+        ++phases;
+        // ---- BFS levels; sm.qn is the queue tail, sm.qbase the endpoint count
+        int qb = 0, qe = n_roots, lvl = L0, levels = 0, n_ep = 0;
+        auto push_col = [&](int2 v) { p.queue[atomicAdd(&sm.qn, 1)] = v; };
+        auto push_end = [&](int v) { p.endpoints[atomicAdd(&sm.qbase, 1)] = v; };
+        for (;;) {
+            const int q = qe - qb;
+            for (int first = 0; first < q; first += T) {
+                tile_load<WR, NC>(p, qb, q, first, T, sm, cnt, nullptr);
+                tile_edges<WR, decltype(push_col), decltype(push_end), NC>(p, T, lvl, q <= T, sm, cnt,
+                                                                           push_col, push_end);
+                __syncthreads();  // sm.off/beg/col/root are reused by the next tile
+            }
+            __syncthreads();
+            const int tail = sm.qn;
+            const int eps = sm.qbase;
+            ++levels;
+            if (tail == qe) { n_ep = eps; break; }  // no vertex inserted
+            if (p.mode == 1 && eps > 0) { n_ep = eps; break; }  // APsB
+            if (levels > nc + 2) { status = -4; n_ep = eps; break; }
+            qb = qe;
+            qe = tail;
+            ++lvl;
+        }
+        levels_total += levels;
+        eps_total += n_ep;
+        if (status) break;
+        if (n_ep == 0) break;  // no augmenting path: maximum (Berge)
+        // ---- Alternate (Algorithm 3) and the row half of FixMatching
+        for (int i = t; i < n_ep; i += T) {
+            int r = __ldcg(&p.endpoints[i]);
+            int steps = 0;
+            while (r != -1) {
+                if (++steps > levels + 2) { atomicCAS(&sm.ok, 0, -4); break; }
+                const int c = __ldcg(&p.pred[r]);
+                if ((unsigned)c >= (unsigned)nc) { atomicCAS(&sm.ok, 0, -7); break; }
+                const int r2 = ld_volatile(&p.cmatch[c]);
+                if (r2 >= 0 && __ldcg(&p.pred[r2]) == c) break;
+                st_volatile(&p.cmatch[c], r);
+                __stcg(&p.rmatch[r], c);
+                cnt.alt++;
+                r = r2;
+            }
+        }
+        __syncthreads();
+        for (int r = t; r < nr; r += T) {
+            const int m = __ldcg(&p.rmatch[r]);
+            if (m == -1) continue;
+            if (m < 0 || __ldcg(&p.cmatch[m]) != r) {
+                __stcg(&p.rmatch[r], -1);
+                cnt.fixes++;
+            }
+        }
+        __syncthreads();
+        if (sm.ok != 0) { status = sm.ok; break; }
+    }
+    card_out = card;
+    phases_out = phases + 1;
+    levels_out = levels_total;
+    eps_out = eps_total;
+    __syncthreads();
+    return status;
+}
+
+// Checks one graph's CSR with one block: col_ptr from 0, monotone, up to nnz
+// (so every later row_idx read is in range), rows in [0, nr).  Returns
+// whether it is valid (same answer in every thread).
+template <bool NC>
+__device__ bool block_check_csr(int nr, int nc, long long nnz, const int32_t* cp, const int32_t* ri, Smem& sm) {
+    if (threadIdx.x == 0) sm.ok = (nr < 0 || nc < 0 || ld_csr<NC>(&cp[0]) != 0 ||
+                                   (long long)ld_csr<NC>(&cp[nc]) != nnz) ? 1 : 0;
+    __syncthreads();
+    bool bad = false;
+    if (sm.ok == 0) {
+        for (int c = threadIdx.x; c < nc; c += blockDim.x)
+            if (ld_csr<NC>(&cp[c + 1]) < ld_csr<NC>(&cp[c])) bad = true;
+    }
+    if (bad) atomicOr(&sm.ok, 1);
+    __syncthreads();
+    if (sm.ok == 0) {
+        for (long long e = threadIdx.x; e < nnz; e += blockDim.x) {
+            const int r = ld_csr<NC>(&ri[e]);
+            if (r < 0 || r >= nr) bad = true;
+        }
+    }
+    if (bad) atomicOr(&sm.ok, 1);
+    __syncthreads();
+    const bool ok = sm.ok == 0;
+    __syncthreads();
+    return ok;
 }
 
 __device__ __forceinline__ void flush_counters(const Params& p, Counters& cnt) {

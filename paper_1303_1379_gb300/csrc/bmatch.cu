@@ -39,8 +39,8 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
     using namespace bmd;
     Ctl* ctl = p.ctl;
     __shared__ Smem sm;
-    if (threadIdx.x == 0) sm.qn = 0;
-    unsigned long long target = 0;
+    if (threadIdx.x == 0) { sm.qn = 0; sm.npush = 0; sm.has_ep = 0; }
+    int bid = 0;  // grid barriers passed
     const unsigned long long t_start = globaltimer();
     const unsigned long long deadline = t_start + (unsigned long long)p.total_ns;
     const bool leader = (blockIdx.x == 0 && threadIdx.x == 0);
@@ -55,11 +55,16 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
     for (;;) {
         // ---- InitBfsArray (+ column half of FixMatching)
         int s = step++;
-        if (leader) { ctl->qcnt[(s + 1) % 3] = 0; ctl->ecnt[(s + 1) % 3] = 0; ctl->tcnt[(s + 1) % 3] = 0; }
+        if (leader) {
+            ctl->qcnt[(s + 1) % 3] = 0;
+            ctl->ecnt[(s + 1) % 3] = 0;
+            ctl->tcnt[(s + 1) % 3] = 0;
+            ctl->ep_phase = 0;
+        }
         step_init<WR>(p, s % 3, cnt, sm);
-        if (!grid_sync(ctl, target, p.wait_ns, deadline, sm, &ctl->qcnt[s % 3], &ctl->ecnt[s % 3])) goto out;
+        if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, &ctl->ecnt[s % 3])) goto out;
         const int n_roots = sm.bc_a;  // unmatched columns with rows: the first queue segment
-        card = p.nc - sm.bc_b;        // all unmatched columns
+        card = p.nc - sm.bc_c;        // all unmatched columns
         if (leader && phases == 0) ctl->initial_card = card;
         if (n_roots == 0) break;  // every column matched
         if (phases >= p.max_phases) {
@@ -69,26 +74,29 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
         ++phases;
 
         // ---- BFS, level by level (Algorithm 1 inner loop)
-        int qb = 0, qe = n_roots, lvl = L0, n_ep = 0, levels = 0, first_ep = 0, last_ep = 0;
+        int qb = 0, qe = n_roots, lvl = L0, levels = 0, first_ep = 0, last_ep = 0;
         for (;;) {
             int s2 = step++;
             if (leader) { ctl->qcnt[(s2 + 1) % 3] = 0; ctl->ecnt[(s2 + 1) % 3] = 0; ctl->tcnt[(s2 + 1) % 3] = 0; }
-            step_expand<WR>(p, qb, qe, lvl, s2 % 3, n_ep, cnt, sm);
-            if (!grid_sync(ctl, target, p.wait_ns, deadline, sm, &ctl->qcnt[s2 % 3], &ctl->ecnt[s2 % 3])) goto out;
-            const int nq = sm.bc_a;
-            n_ep += sm.bc_b;
+            step_expand<WR>(p, qb, qe, lvl, s2 % 3, cnt, sm);
+            if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
+            const int nq = sm.bc_a;           // columns inserted at this level
+            const bool found = sm.bc_b > 0;   // some block claimed an endpoint
             ++levels;
-            if (sm.bc_b > 0) {
+            if (found) {
                 if (first_ep == 0) first_ep = levels;
                 last_ep = levels;
             }
             ins_total += nq;
-            if (nq == 0) break;                  // no vertex inserted
-            if (p.mode == 1 && n_ep > 0) break;  // APsB: stop at the first level with a path
+            if (nq == 0) break;              // no vertex inserted
+            if (p.mode == 1 && found) break;  // APsB: stop at the first level with a path
             qb = qe;
             qe += nq;
             ++lvl;
         }
+        if (threadIdx.x == 0) sm.bc_c = ld_volatile(&ctl->ep_phase);  // all appends precede the barrier
+        __syncthreads();
+        const int n_ep = sm.bc_c;
         levels_total += levels;
         if (levels > levels_max) levels_max = levels;
         eps_total += n_ep;
@@ -105,16 +113,16 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
 
         if (p.bfs_only) {
             step_release_endpoints(p, n_ep);
-            if (!grid_sync(ctl, target, p.wait_ns, deadline, sm, nullptr, nullptr)) goto out;
+            if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
             break;
         }
         if (n_ep == 0) break;  // no augmenting path: the matching is maximum (Berge)
 
         // ---- Alternate, then the row half of FixMatching
         step_alternate(p, n_ep, levels + 2, cnt);
-        if (!grid_sync(ctl, target, p.wait_ns, deadline, sm, nullptr, nullptr)) goto out;
+        if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
         step_fix_rows(p, cnt);
-        if (!grid_sync(ctl, target, p.wait_ns, deadline, sm, nullptr, nullptr)) goto out;
+        if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
     }
 out:
     flush_counters(p, cnt);
@@ -135,19 +143,19 @@ out:
 template <bool WR>
 __global__ void __launch_bounds__(1024) k_init(Params p, int slot) {
     __shared__ bmd::Smem sm;
-    if (threadIdx.x == 0) sm.qn = 0;
+    if (threadIdx.x == 0) { sm.qn = 0; sm.npush = 0; sm.has_ep = 0; }
     __syncthreads();
     Counters cnt{0, 0, 0, 0, 0};
     bmd::step_init<WR>(p, slot, cnt, sm);
     bmd::flush_counters(p, cnt);
 }
 template <bool WR>
-__global__ void __launch_bounds__(1024) k_expand(Params p, int qb, int qe, int lvl, int slot, int ebase) {
+__global__ void __launch_bounds__(1024) k_expand(Params p, int qb, int qe, int lvl, int slot) {
     __shared__ bmd::Smem sm;
-    if (threadIdx.x == 0) sm.qn = 0;
+    if (threadIdx.x == 0) { sm.qn = 0; sm.npush = 0; sm.has_ep = 0; }
     __syncthreads();
     Counters cnt{0, 0, 0, 0, 0};
-    bmd::step_expand<WR>(p, qb, qe, lvl, slot, ebase, cnt, sm);
+    bmd::step_expand<WR>(p, qb, qe, lvl, slot, cnt, sm);
     bmd::flush_counters(p, cnt);
 }
 __global__ void __launch_bounds__(1024) k_alternate(Params p, int n_ep, int cap) {
@@ -247,7 +255,7 @@ struct bm_ctx {
     int32_t* level = nullptr;
     int32_t* root = nullptr;
     int32_t* pred = nullptr;
-    int32_t* queue = nullptr;
+    int2* queue = nullptr;
     int32_t* endpoints = nullptr;
     int32_t* profile = nullptr;  // kProfileCap phases x 4
     Ctl* ctl = nullptr;
@@ -374,12 +382,17 @@ int32_t run_host_loop(bm_ctx* ctx, const Params& p) {
         BM_CUDA(ctx, cudaMemsetAsync(&ctx->ctl->tcnt[slot], 0, sizeof(int32_t), st));
         return BM_OK;
     };
+    auto clear_phase = [&]() -> int32_t {
+        BM_CUDA(ctx, cudaMemsetAsync(&ctx->ctl->ep_phase, 0, sizeof(int32_t), st));
+        return BM_OK;
+    };
     int32_t rc = sync_ctl(ctx);
     if (rc) return rc;
     if (h->err) return h->err;
     for (;;) {
         int s = step++;
         if ((rc = clear_slot(s % 3))) return rc;
+        if ((rc = clear_phase())) return rc;
         k_init<WR><<<gb, blk, 0, st>>>(p, s % 3);
         BM_CUDA(ctx, cudaGetLastError());
         if ((rc = sync_ctl(ctx))) return rc;
@@ -396,13 +409,14 @@ int32_t run_host_loop(bm_ctx* ctx, const Params& p) {
             int s2 = step++;
             if ((rc = clear_slot(s2 % 3))) return rc;
             const int g = grid_for(ctx, qe - qb);
-            k_expand<WR><<<g, blk, 0, st>>>(p, qb, qe, lvl, s2 % 3, n_ep);
+            k_expand<WR><<<g, blk, 0, st>>>(p, qb, qe, lvl, s2 % 3);
             BM_CUDA(ctx, cudaGetLastError());
             if ((rc = sync_ctl(ctx))) return rc;
             const int nq = h->qcnt[s2 % 3];
-            n_ep += h->ecnt[s2 % 3];
+            const int new_ep = h->ep_phase - n_ep;
+            n_ep = h->ep_phase;
             ++levels;
-            if (h->ecnt[s2 % 3] > 0) {
+            if (new_ep > 0) {
                 if (first_ep == 0) first_ep = levels;
                 last_ep = levels;
             }
@@ -565,7 +579,7 @@ int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* co
     size_t off_rt = off_lv + al(4 * nc1);
     size_t off_pd = off_rt + al(4 * nc1);
     size_t off_q = off_pd + al(4 * nr1);
-    size_t off_ep = off_q + al(4 * nc1);
+    size_t off_ep = off_q + al(8 * nc1);
     size_t off_pf = off_ep + al(4 * nr1);
     size_t off_cp = off_pf + al(4 * 4 * (size_t)kProfileCap);
     size_t total = off_cp;
@@ -593,7 +607,7 @@ int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* co
     ctx->level = (int32_t*)(a + off_lv);
     ctx->root = (int32_t*)(a + off_rt);
     ctx->pred = (int32_t*)(a + off_pd);
-    ctx->queue = (int32_t*)(a + off_q);
+    ctx->queue = (int2*)(a + off_q);
     ctx->endpoints = (int32_t*)(a + off_ep);
     ctx->profile = (int32_t*)(a + off_pf);
     if (own) {
@@ -893,7 +907,7 @@ extern "C" int32_t bm_match_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
     const size_t off_rt = off_lv + round256(4 * nc);
     const size_t off_pd = off_rt + round256(4 * nc);
     const size_t off_q = off_pd + round256(4 * nr);
-    const size_t off_ep = off_q + round256(4 * nc);
+    const size_t off_ep = off_q + round256(8 * nc);
     const size_t need = off_ep + round256(4 * nr);
     if (need > (size_t)BM_NOALLOC_SCRATCH_BYTES) return BM_ERR_TOO_LARGE;
 
@@ -917,7 +931,7 @@ extern "C" int32_t bm_match_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
     p.level = (int32_t*)(s + off_lv);
     p.root = (int32_t*)(s + off_rt);
     p.pred = (int32_t*)(s + off_pd);
-    p.queue = (int32_t*)(s + off_q);
+    p.queue = (int2*)(s + off_q);
     p.endpoints = (int32_t*)(s + off_ep);
     p.ctl = ctl;
     p.mode = BM_APFB;
