@@ -47,6 +47,8 @@ WORKLOADS = {
     "uniform10k": "uniform 10,000 x 10,000, column degree U{1..8}, int32 CSR, empty initial "
                   "matching, seed 0",
 }
+for _k in list(WORKLOADS):
+    WORKLOADS[_k + "-rcp"] = WORKLOADS[_k] + "; rows and columns randomly permuted (seed 5)"
 METRIC = "ms to max matching, GTEPS and % HBM roofline; batched graphs/s vs one-by-one"
 L2_FLUSH_BYTES = 256 << 20
 
@@ -61,6 +63,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-distinct", type=int, default=48)
     return ap.parse_args()
 
 
@@ -193,6 +198,7 @@ def load_workload(name):
 
 
 def golden_max(name):
+    name = name[:-4] if name.endswith("-rcp") else name  # permutation keeps |M|
     try:
         with open(os.path.join(ROOT, "tests", "golden", "workloads.txt")) as f:
             for line in f:
@@ -213,7 +219,7 @@ def run_reference(args):
         return 0
     import oracle
     g = load_workload(args.workload)
-    empty = args.workload == "uniform10k"
+    empty = args.workload.startswith("uniform10k")
     if empty:
         rm0, cm0 = oracle.empty_matching(g.n_rows, g.n_cols)
     else:
@@ -350,6 +356,91 @@ def batched_cpu_baseline(b, batch_cards):
             f"over all host threads ({dt:.1f} s)", "cardinalities_agree": agree}
 
 
+# ------------------------------------------------------------------ served workload
+SERVE_WORKLOAD = ("Poisson stream of matching requests, each a uniform (column degree "
+                  "U{1..round(2mu-1)}) or R-MAT (scale ceil(log2 n), n*mu samples, ids >= n "
+                  "rejected, duplicates removed) graph, 50/50, rows log-uniform in [1,000, "
+                  "1,000,000], columns = rows x U[0.8, 1.25], mu ~ U[3, 16], seed 4; greedy "
+                  "start per request")
+
+
+def serve_request_pool(n_distinct, seed=4):
+    """The distinct request graphs (request i of the stream uses graph i % n)."""
+    import numpy as np
+    from paper_1303_1379_gb300 import synth
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_distinct):
+        nr = int(np.exp(rng.uniform(np.log(1e3), np.log(1e6))))
+        nc = max(1, int(round(nr * rng.uniform(0.8, 1.25))))
+        mu = rng.uniform(3, 16)
+        if i % 2 == 0:
+            g = synth.uniform_graph(nr, nc, max(1, int(round(2 * mu - 1))), seed=seed * 100000 + i)
+        else:
+            n = max(nr, nc)
+            g = synth.rmat_graph(int(np.ceil(np.log2(n))), int(n * mu), seed=seed * 100000 + i, n=n)
+        out.append(g)
+    return out
+
+
+def bench_serving(args, torch, bmatch):
+    import numpy as np
+    t_gen = time.perf_counter()
+    graphs = serve_request_pool(args.serve_distinct)
+    t_gen = time.perf_counter() - t_gen
+    host = [(g.n_rows, g.n_cols, torch.from_numpy(g.col_ptr).pin_memory(),
+             torch.from_numpy(g.row_idx).pin_memory(), g.nnz) for g in graphs]
+    N = args.serve_requests
+    mean_edges = float(np.mean([h[4] for h in host]))
+    srv = bmatch.Server(pool_bytes=32 << 30)
+
+    def run(rate):
+        """rate None: all N submitted at once (closed loop saturation)."""
+        rng = np.random.default_rng(44)
+        gaps = rng.exponential(1.0 / rate, N) if rate else np.zeros(N)
+        t0 = time.perf_counter()
+        arrival = t0 + np.cumsum(gaps)
+        ids = []
+        for i in range(N):
+            if rate:
+                while time.perf_counter() < arrival[i]:
+                    pass
+            nr, nc, cp, ri, _ = host[i % len(host)]
+            ids.append(srv.submit(nr, nc, cp, ri))
+        lat, cards = [], []
+        for rid in ids:
+            info = srv.wait(rid, timeout_s=120)
+            if info["status"] != 0:
+                raise SystemExit(f"served request failed: {info}")
+            lat.append(info["latency_ns"] / 1e6)
+            cards.append(info["card"])
+            srv.release(rid)
+        span = time.perf_counter() - t0
+        return {"requests": N, "offered_rps": rate, "achieved_rps": N / span,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "edges_per_s": N * mean_edges / span, "span_s": span}, cards
+
+    sat, cards = run(None)
+    lam = sat["achieved_rps"]
+    runs = {"closed_loop": sat}
+    for frac in (0.5, 0.9):
+        r, c2 = run(frac * lam)
+        runs[f"poisson_{frac}"] = r
+        if c2 != cards:
+            raise SystemExit("served results differ between runs")
+    st = srv.stats()
+    srv.close()
+    distinct = {}
+    for i, c in enumerate(cards[:len(host)]):
+        distinct[i] = c
+    return {"workload": SERVE_WORKLOAD, "distinct_request_graphs": len(host),
+            "requests_per_run": N, "mean_edges_per_request": mean_edges, "generate_s": round(t_gen, 1),
+            "lambda_max_rps": lam, "runs": runs, "worker_grid": st["grid"], "worker_block": st["block"],
+            "note": "request graphs recycled from the distinct set (host generation of every request "
+                    "would dominate the run); each request is uploaded, matched and released on its own"}, \
+        graphs, distinct
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import numpy as np
@@ -374,7 +465,7 @@ def run_ours(args):
     wr = m.options.bfs == bmatch.BM_GPUBFS_WR
 
     # initial matching (untimed, as in the paper): GPU cheap matching, saved
-    empty = args.workload == "uniform10k"
+    empty = args.workload.startswith("uniform10k")
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
@@ -497,6 +588,18 @@ def run_ours(args):
         batched, bgraphs, bcards = bench_batched(args, torch, bmatch, stream, flush)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             batched["cpu_baseline"] = batched_cpu_baseline(bgraphs, bcards)
+    served = None
+    if not args.no_serve and world == 1:
+        served, sgraphs, scards = bench_serving(args, torch, bmatch)
+        if not args.no_cpu_baseline:
+            import oracle
+            t = time.perf_counter()
+            ok = all(oracle.hopcroft_karp(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)[2] == scards[i]
+                     for i, g in enumerate(sgraphs[:8]))
+            dt = time.perf_counter() - t
+            served["cpu_baseline"] = {"value": 8 / dt, "unit": "requests/s", "cores": 1,
+                                      "kind": "oracle", "sample": "first 8 distinct request graphs, "
+                                      "Hopcroft-Karp from empty, one core", "cardinalities_agree": ok}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -523,6 +626,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched": batched,
+        "served": served,
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
         "wall_s": wall,

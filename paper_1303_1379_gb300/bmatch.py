@@ -32,6 +32,32 @@ BM_APFB, BM_APSB = 0, 1
 BM_GPUBFS, BM_GPUBFS_WR = 0, 1
 BM_DRIVER_PERSISTENT, BM_DRIVER_HOST = 0, 1
 
+class bm_server_options(ctypes.Structure):
+    _fields_ = [("pool_bytes", ctypes.c_int64), ("reserve_bytes", ctypes.c_int64),
+                ("ring_slots", ctypes.c_int32), ("block_size", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("bfs", ctypes.c_int32), ("keep_results", ctypes.c_int32),
+                ("idle_timeout_ns", ctypes.c_int64), ("poll_interval_us", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("reserved", ctypes.c_int64 * 4)]
+
+
+class bm_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("card", ctypes.c_int32),
+                ("phases", ctypes.c_int32), ("latency_ns", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 2)]
+
+
+class bm_server_stats(ctypes.Structure):
+    _fields_ = [("pending", ctypes.c_int64), ("inflight", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("worker_launches", ctypes.c_int64), ("pool_bytes", ctypes.c_int64),
+                ("pool_used", ctypes.c_int64), ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 2)]
+
+
+BM_REQ_PENDING, BM_REQ_UPLOADING, BM_REQ_RUNNING, BM_REQ_DONE, BM_REQ_CANCELLED = range(5)
+
+
 class bm_batch_desc(ctypes.Structure):
     _fields_ = [("n_graphs", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("n_rows", ctypes.c_void_p), ("n_cols", ctypes.c_void_p),
@@ -56,7 +82,9 @@ EXPORTS = ("bm_default_options", "bm_version", "bm_status_string", "bm_create", 
            "bm_set_options", "bm_greedy", "bm_set_matching", "bm_get_matching", "bm_match",
            "bm_match_host", "bm_bfs", "bm_phase_profile", "bm_destroy", "bm_batch_create",
            "bm_batch_set_options", "bm_batch_match", "bm_batch_graph_status", "bm_batch_autotune",
-           "bm_batch_destroy", "bm_match_noalloc")
+           "bm_batch_destroy", "bm_match_noalloc", "bm_server_default_options", "bm_server_create",
+           "bm_server_submit", "bm_server_poll", "bm_server_wait", "bm_server_cancel",
+           "bm_server_fetch", "bm_server_release", "bm_server_get_stats", "bm_server_destroy")
 
 
 class bm_options(ctypes.Structure):
@@ -151,6 +179,28 @@ def load(build_if_missing: bool = True):
             lib.bm_batch_autotune.restype = ctypes.c_int32
             lib.bm_batch_destroy.argtypes = [VP]
             lib.bm_batch_destroy.restype = ctypes.c_int32
+            lib.bm_server_default_options.argtypes = [ctypes.POINTER(bm_server_options)]
+            lib.bm_server_default_options.restype = None
+            lib.bm_server_create.argtypes = [ctypes.POINTER(bm_server_options), ctypes.POINTER(VP)]
+            lib.bm_server_create.restype = ctypes.c_int32
+            lib.bm_server_submit.argtypes = [VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, VP,
+                                             VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
+            lib.bm_server_submit.restype = ctypes.c_int32
+            lib.bm_server_poll.argtypes = [VP, ctypes.c_int64, ctypes.POINTER(bm_request_info)]
+            lib.bm_server_poll.restype = ctypes.c_int32
+            lib.bm_server_wait.argtypes = [VP, ctypes.c_int64, ctypes.c_int64,
+                                           ctypes.POINTER(bm_request_info)]
+            lib.bm_server_wait.restype = ctypes.c_int32
+            lib.bm_server_cancel.argtypes = [VP, ctypes.c_int64]
+            lib.bm_server_cancel.restype = ctypes.c_int32
+            lib.bm_server_fetch.argtypes = [VP, ctypes.c_int64, VP, VP]
+            lib.bm_server_fetch.restype = ctypes.c_int32
+            lib.bm_server_release.argtypes = [VP, ctypes.c_int64]
+            lib.bm_server_release.restype = ctypes.c_int32
+            lib.bm_server_get_stats.argtypes = [VP, ctypes.POINTER(bm_server_stats)]
+            lib.bm_server_get_stats.restype = ctypes.c_int32
+            lib.bm_server_destroy.argtypes = [VP]
+            lib.bm_server_destroy.restype = ctypes.c_int32
             lib.bm_destroy.argtypes = [VP]
             lib.bm_destroy.restype = ctypes.c_int32
             _lib = lib
@@ -423,3 +473,77 @@ class Batch:
                                            reps, ms, ctypes.byref(best)), "bm_batch_autotune")
         self.options.block_size, self.options.blocks_per_sm = candidates[best.value]
         return best.value, list(ms)
+
+
+class Server:
+    """Continuous-batching matching server (bm_server_*).  Requests are host
+    CSR arrays (numpy int32 or pinned CPU tensors) kept alive by this object
+    until they are released."""
+
+    def __init__(self, **options):
+        self._lib = load()
+        o = bm_server_options()
+        self._lib.bm_server_default_options(ctypes.byref(o))
+        for k, v in options.items():
+            if not hasattr(o, k):
+                raise KeyError(k)
+            setattr(o, k, v)
+        self.options = o
+        h = VP()
+        _check(self._lib.bm_server_create(ctypes.byref(o), ctypes.byref(h)), "bm_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, n_rows, n_cols, col_ptr, row_idx, greedy=True) -> int:
+        rid = ctypes.c_int64(0)
+        nnz = int(col_ptr[-1]) if n_cols > 0 else 0
+        _check(self._lib.bm_server_submit(self._h, int(n_rows), int(n_cols), nnz, _host_ptr(col_ptr),
+                                          _host_ptr(row_idx) if nnz else None, int(bool(greedy)),
+                                          ctypes.byref(rid)), "bm_server_submit")
+        self._keep[rid.value] = (col_ptr, row_idx)
+        return rid.value
+
+    def poll(self, rid) -> dict:
+        info = bm_request_info()
+        _check(self._lib.bm_server_poll(self._h, int(rid), ctypes.byref(info)), "bm_server_poll")
+        return {k: getattr(info, k) for k, _ in info._fields_ if k != "reserved"}
+
+    def wait(self, rid, timeout_s=60.0) -> dict:
+        info = bm_request_info()
+        rc = self._lib.bm_server_wait(self._h, int(rid), int(timeout_s * 1e9), ctypes.byref(info))
+        _check(rc, "bm_server_wait")
+        return {k: getattr(info, k) for k, _ in info._fields_ if k != "reserved"}
+
+    def cancel(self, rid):
+        return int(self._lib.bm_server_cancel(self._h, int(rid)))
+
+    def fetch(self, rid, rmatch, cmatch):
+        _check(self._lib.bm_server_fetch(self._h, int(rid), _host_ptr(rmatch), _host_ptr(cmatch)),
+               "bm_server_fetch")
+
+    def release(self, rid):
+        _check(self._lib.bm_server_release(self._h, int(rid)), "bm_server_release")
+        self._keep.pop(int(rid), None)
+
+    def stats(self) -> dict:
+        st = bm_server_stats()
+        _check(self._lib.bm_server_get_stats(self._h, ctypes.byref(st)), "bm_server_get_stats")
+        return {k: getattr(st, k) for k, _ in st._fields_ if k != "reserved"}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bm_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -229,6 +229,10 @@ def permute_graph(g: Graph, seed: int) -> Graph:
 # The five workloads of the benchmark (sizes of the paper's instance classes;
 # see the design notes for why each stands in for which matrices).
 def workload(name: str) -> Graph:
+    """Named workloads; a "-rcp" suffix applies the random row and column
+    permutation of Section 4 (seed 5)."""
+    if name.endswith("-rcp"):
+        return permute_graph(workload(name[:-4]), seed=5)
     if name == "uniform10k":
         return uniform_graph(10_000, 10_000, 8, seed=0)
     if name == "rmat21":

@@ -1,0 +1,116 @@
+"""Serving (continuous batching) against the oracle and against requests run
+alone: |M| is exact whether a request runs alone or in a mix that arrives
+while others are on the GPU, admission respects the memory pool, and bad or
+oversized requests are reported without disturbing the others."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1303_1379_gb300 import bmatch, synth
+
+from helpers import assert_maximum, csr_from_edges
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def mixed_requests(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nr = int(np.exp(rng.uniform(np.log(50), np.log(20000))))
+        nc = max(1, int(round(nr * rng.uniform(0.8, 1.25))))
+        mu = rng.uniform(3, 16)
+        if i % 2 == 0:
+            g = synth.uniform_graph(nr, nc, max(1, int(round(2 * mu - 1))), seed=1000 + i)
+        else:
+            n = max(nr, nc)
+            scale = int(np.ceil(np.log2(max(n, 2))))
+            g = synth.rmat_graph(scale, int(n * mu), seed=1000 + i, n=n)
+        out.append(g)
+    return out
+
+
+def test_results_same_alone_and_in_the_mix():
+    reqs = mixed_requests(40, seed=4)
+    want = [oracle.hopcroft_karp(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)[2] for g in reqs]
+    with bmatch.Server(keep_results=1, pool_bytes=1 << 30) as srv:
+        # alone: one at a time
+        alone = []
+        for g in reqs[:10]:
+            rid = srv.submit(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+            info = srv.wait(rid)
+            assert info["state"] == bmatch.BM_REQ_DONE and info["status"] == 0
+            alone.append(info["card"])
+            srv.release(rid)
+        # the mix: all submitted at once, arriving while others run
+        ids = [srv.submit(g.n_rows, g.n_cols, g.col_ptr, g.row_idx) for g in reqs]
+        for k, (g, rid) in enumerate(zip(reqs, ids)):
+            info = srv.wait(rid)
+            assert info["status"] == 0 and info["card"] == want[k]
+            rm = np.empty(g.n_rows, np.int32)
+            cm = np.empty(g.n_cols, np.int32)
+            srv.fetch(rid, rm, cm)
+            assert_maximum(g, rm, cm, info["card"], want[k])
+            srv.release(rid)
+        assert alone == want[:10]
+        st = srv.stats()
+        assert st["completed"] == 50 and st["pool_used"] == 0
+
+
+def test_admission_waits_for_pool_memory_and_rejects_oversized():
+    reqs = mixed_requests(12, seed=9)
+    need = max(4 * (g.nnz + 6 * g.n_cols + 3 * g.n_rows) for g in reqs)
+    # a pool that holds only about two requests at a time
+    with bmatch.Server(pool_bytes=3 * need, ring_slots=4) as srv:
+        big = synth.uniform_graph(400000, 400000, 8, seed=2)  # far beyond the pool
+        rid_big = srv.submit(big.n_rows, big.n_cols, big.col_ptr, big.row_idx)
+        ids = [srv.submit(g.n_rows, g.n_cols, g.col_ptr, g.row_idx) for g in reqs]
+        info = srv.wait(rid_big)
+        assert info["status"] == bmatch.BM_ERR_TOO_LARGE
+        for g, rid in zip(reqs, ids):
+            info = srv.wait(rid)
+            assert info["status"] == 0
+            assert info["card"] == oracle.hopcroft_karp(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)[2]
+        st = srv.stats()
+        assert st["rejected"] == 1 and st["pool_used"] == 0
+
+
+def test_malformed_request_and_cancel():
+    good = synth.uniform_graph(3000, 3000, 5, seed=3)
+    bad_ri = good.row_idx.copy()
+    bad_ri[17] = 10 ** 7
+    with bmatch.Server(pool_bytes=1 << 28) as srv:
+        rid_bad = srv.submit(good.n_rows, good.n_cols, good.col_ptr, bad_ri)
+        bad_cp = good.col_ptr.copy()
+        bad_cp[5] = bad_cp[7] + 3
+        rid_bad2 = srv.submit(good.n_rows, good.n_cols, bad_cp, good.row_idx)
+        rid_ok = srv.submit(good.n_rows, good.n_cols, good.col_ptr, good.row_idx)
+        assert srv.wait(rid_bad)["status"] == bmatch.BM_ERR_INVALID_CSR
+        assert srv.wait(rid_bad2)["status"] == bmatch.BM_ERR_INVALID_CSR
+        assert srv.wait(rid_ok)["card"] == oracle.hopcroft_karp(good.n_rows, good.n_cols,
+                                                                good.col_ptr, good.row_idx)[2]
+    # cancellation of requests that have not been admitted: a one-slot ring keeps them pending
+    with bmatch.Server(pool_bytes=1 << 28, ring_slots=1) as srv:
+        ids = [srv.submit(good.n_rows, good.n_cols, good.col_ptr, good.row_idx) for _ in range(6)]
+        cancelled = [rid for rid in ids[2:] if srv.cancel(rid) == 0]
+        for rid in ids:
+            info = srv.wait(rid)
+            if rid in cancelled:
+                assert info["state"] == bmatch.BM_REQ_CANCELLED
+            else:
+                assert info["state"] == bmatch.BM_REQ_DONE and info["status"] == 0
+
+
+def test_idle_workers_leave_and_come_back():
+    g = synth.uniform_graph(2000, 2000, 4, seed=5)
+    want = oracle.hopcroft_karp(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)[2]
+    with bmatch.Server(pool_bytes=1 << 26, idle_timeout_ns=2_000_000) as srv:
+        for _ in range(3):
+            rid = srv.submit(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+            assert srv.wait(rid)["card"] == want
+            srv.release(rid)
+            time.sleep(0.05)  # longer than the idle timeout: the workers leave
+        assert srv.stats()["worker_launches"] >= 2

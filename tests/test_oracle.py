@@ -276,3 +276,18 @@ def test_bfs_levels_against_brute_force_distances():
             assert level[c] == (1 if dist[c] == INF else 2 + dist[c])
         want = sorted({r for r, c in edges if dist[c] < INF and rm[r] == -1})
         assert np.flatnonzero(reached).tolist() == want
+
+
+def test_random_permutation_keeps_the_maximum():
+    """Section 4's RCP instances: permuting rows and columns changes the
+    difficulty, never the maximum matching size."""
+    for g in (synth.uniform_graph(2000, 1800, 5, seed=3), synth.stencil_graph(40, 160, 0.05, seed=2),
+              synth.rmat_graph(11, 15000, seed=7)):
+        h = synth.permute_graph(g, seed=5)
+        assert oracle.csr_check(h.n_rows, h.n_cols, h.col_ptr, h.row_idx) == 0
+        assert h.nnz == g.nnz
+        a = oracle.hopcroft_karp(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)[2]
+        b = oracle.hopcroft_karp(h.n_rows, h.n_cols, h.col_ptr, h.row_idx)[2]
+        assert a == b
+    p = synth.permutation(1000, 5, 0)
+    assert sorted(p.tolist()) == list(range(1000)) and not np.array_equal(p, np.arange(1000))
