@@ -77,10 +77,17 @@ def dist_env():
 
 
 def source_hash() -> str:
+    """Hash of the sources that make up the persistent matching kernel: the
+    device header and the k_match kernel body (other kernels in the same file
+    do not change it)."""
     h = hashlib.sha256()
-    for f in ("paper_1303_1379_gb300/csrc/bmatch.cu", "paper_1303_1379_gb300/csrc/bm_device.cuh"):
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_1303_1379_gb300/csrc/bm_device.cuh"), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_1303_1379_gb300/csrc/bmatch.cu"), "r") as fh:
+        text = fh.read()
+    start = text.find("// One launch per match")
+    end = text.find("// ---- per-step kernels")
+    h.update(text[start:end].encode())
     return h.hexdigest()[:16]
 
 

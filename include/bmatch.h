@@ -305,8 +305,9 @@ BM_API int32_t bm_batch_destroy(bm_batch *b);
  * matches one request at a time (cheap matching + Algorithm 1, the batched
  * path's block routine) and reports |M| back through host-mapped memory.
  * Requests that arrive while others run are taken by whichever worker frees
- * first.  Workers leave after idle_timeout_ns without work and are relaunched
- * when work arrives; every device-side wait is bounded.
+ * first.  Workers leave together once no worker has been busy for
+ * idle_timeout_ns and are relaunched when work arrives; every device-side wait
+ * is bounded.
  */
 typedef struct bm_server_options {
     int64_t pool_bytes;      /* device pool for resident requests; 0 = free memory - reserve     */
@@ -317,7 +318,7 @@ typedef struct bm_server_options {
     int32_t mode;            /* BM_APFB (default) / BM_APSB                                      */
     int32_t bfs;             /* BM_GPUBFS_WR (default) / BM_GPUBFS                               */
     int32_t keep_results;    /* 1: keep each request's matching until bm_server_release          */
-    int64_t idle_timeout_ns; /* workers leave after this long without work (default 20 ms)       */
+    int64_t idle_timeout_ns; /* workers leave when no block has been busy this long (default 50 ms) */
     int32_t poll_interval_us;/* scheduler sleep when idle (default 5)                             */
     int32_t reserved0;
     int64_t reserved[4];

@@ -505,27 +505,110 @@ __device__ __forceinline__ void step_release_endpoints(const Params& p, int n_ep
 }
 
 // ------------------------------------------------------------------ one graph, one block
+// InitBfsArray over all columns of one graph by one block (4 columns per
+// thread in flight): column half of FixMatching, level / root init, unmatched
+// columns with rows appended to the queue as roots.  Returns the roots in
+// sm.qn; free_total / iso_free get all unmatched columns and those without rows.
+template <bool WR, bool NC>
+__device__ __forceinline__ void block_full_init(const Params& p, Smem& sm, Counters& cnt, int& free_total,
+                                                int& iso_free) {
+    const int T = blockDim.x, t = threadIdx.x, nc = p.nc;
+    if (t == 0) { sm.qn = 0; sm.qbase = 0; sm.total = 0; sm.tile = 0; }
+    __syncthreads();
+    int nfree = 0, niso = 0;
+    for (int base = 0; base < nc; base += 4 * T) {
+        int c[4], r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            c[u] = base + u * T + t;
+            r[u] = c[u] < nc ? __ldcg(&p.cmatch[c[u]]) : -3;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (c[u] >= nc) continue;
+            if (r[u] >= 0 && __ldcg(&p.rmatch[r[u]]) != c[u]) {
+                __stcg(&p.cmatch[c[u]], -1);
+                r[u] = -1;
+                cnt.fixes++;
+            }
+            const bool is_free = r[u] < 0;
+            __stcg(&p.level[c[u]], is_free ? L0 : L0 - 1);
+            if (WR) __stcg(&p.root[c[u]], is_free ? c[u] : -1);
+            if (is_free) {
+                ++nfree;
+                if (ld_csr<NC>(&p.col_ptr[c[u] + 1]) > ld_csr<NC>(&p.col_ptr[c[u]]))
+                    p.queue[atomicAdd(&sm.qn, 1)] = make_int2(c[u], c[u]);
+                else
+                    ++niso;
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        nfree += __shfl_down_sync(FULL, nfree, s);
+        niso += __shfl_down_sync(FULL, niso, s);
+    }
+    if ((t & 31) == 0 && nfree) atomicAdd(&sm.total, nfree);
+    if ((t & 31) == 0 && niso) atomicAdd(&sm.tile, niso);
+    __syncthreads();
+    free_total = sm.total;
+    iso_free = sm.tile;
+    __syncthreads();
+}
+
 // The whole method on one graph by one block (batched and served paths):
 // optional cheap matching, then Algorithm 1 with the steps separated by
-// __syncthreads; queue tail, endpoint count and free-column count live in
-// shared memory (sm.qn, sm.qbase, sm.total).  Returns the graph's status.
+// __syncthreads; queue tail and endpoint count live in shared memory (sm.qn,
+// sm.qbase).  With GPUBFS-WR and one endpoint per root, the search trees are
+// disjoint and each holds at most one endpoint, so Alternate's walks never
+// meet: every walk reaches its root and FixMatching has nothing to repair.
+// That mode therefore skips the FixMatching passes and, instead of
+// re-initialising every column each phase, resets the columns the last
+// search visited and keeps the roots that are still unmatched (work per phase
+// proportional to the search, not to n_cols).  The other modes run the full
+// passes.  Returns the graph's status.
 template <bool WR, bool NC>
 __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters& cnt, int& card_out,
                                  int& phases_out, long long& levels_out, long long& eps_out) {
     const int T = blockDim.x;
     const int t = threadIdx.x;
     const int nr = p.nr, nc = p.nc;
+    const bool incremental = WR && p.one_ep;
     if (t == 0) sm.ok = 0;
-    // ---- cheap matching (Section 4): unmatched columns claim their first free row
+    // ---- rows whose column does not point back are unmatched (row half of FixMatching)
+    for (int r = t; r < nr; r += T) {
+        const int m = __ldcg(&p.rmatch[r]);
+        if (m != -1 && (m < 0 || m >= nc || __ldcg(&p.cmatch[m]) != r)) __stcg(&p.rmatch[r], -1);
+    }
+    __syncthreads();
+    // ---- cheap matching (Section 4): unmatched columns claim their first free row;
+    // first tries of 4 columns per thread in flight, then the rest of each list
     if (greedy) {
-        for (int c = t; c < nc; c += T) {
-            if (__ldcg(&p.cmatch[c]) != -1) continue;
-            const int end = ld_csr<NC>(&p.col_ptr[c + 1]);
-            for (int e = ld_csr<NC>(&p.col_ptr[c]); e < end; ++e) {
-                const int r = ld_csr<NC>(&p.row_idx[e]);
-                if (ld_volatile(&p.rmatch[r]) == -1 && atomicCAS(&p.rmatch[r], -1, c) == -1) {
-                    p.cmatch[c] = r;
-                    break;
+        for (int base = 0; base < nc; base += 4 * T) {
+            int c[4], b[4], e[4], r0[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                c[u] = base + u * T + t;
+                b[u] = e[u] = 0;
+                if (c[u] < nc && __ldcg(&p.cmatch[c[u]]) == -1) {
+                    b[u] = ld_csr<NC>(&p.col_ptr[c[u]]);
+                    e[u] = ld_csr<NC>(&p.col_ptr[c[u] + 1]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) r0[u] = b[u] < e[u] ? ld_csr<NC>(&p.row_idx[b[u]]) : -1;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (b[u] >= e[u]) continue;
+                int pos = b[u];
+                int r = r0[u];
+                for (;;) {
+                    if (ld_volatile(&p.rmatch[r]) == -1 && atomicCAS(&p.rmatch[r], -1, c[u]) == -1) {
+                        p.cmatch[c[u]] = r;
+                        break;
+                    }
+                    if (++pos >= e[u]) break;
+                    r = ld_csr<NC>(&p.row_idx[pos]);
                 }
             }
         }
@@ -534,37 +617,17 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
     const int max_phases = (nr < nc ? nr : nc) + 2;
     int phases = 0, card = 0, status = 0;
     long long levels_total = 0, eps_total = 0;
+    int free_total = 0, iso_free = 0;
+    block_full_init<WR, NC>(p, sm, cnt, free_total, iso_free);
+    int n_roots = sm.qn;
     for (;;) {
-        // ---- InitBfsArray (+ column half of FixMatching)
-        if (t == 0) { sm.qn = 0; sm.qbase = 0; sm.total = 0; }
-        __syncthreads();
-        int nfree = 0;
-        for (int c = t; c < nc; c += T) {
-            int r = __ldcg(&p.cmatch[c]);
-            if (r >= 0 && __ldcg(&p.rmatch[r]) != c) {
-                __stcg(&p.cmatch[c], -1);
-                r = -1;
-                cnt.fixes++;
-            }
-            const bool is_free = r < 0;
-            __stcg(&p.level[c], is_free ? L0 : L0 - 1);
-            if (WR) __stcg(&p.root[c], is_free ? c : -1);
-            if (is_free) {
-                ++nfree;
-                if (ld_csr<NC>(&p.col_ptr[c + 1]) > ld_csr<NC>(&p.col_ptr[c]))
-                    p.queue[atomicAdd(&sm.qn, 1)] = make_int2(c, c);
-            }
-        }
-#pragma unroll
-        for (int s = 16; s >= 1; s >>= 1) nfree += __shfl_down_sync(FULL, nfree, s);
-        if ((t & 31) == 0 && nfree) atomicAdd(&sm.total, nfree);
-        __syncthreads();
-        const int n_roots = sm.qn;
-        card = nc - sm.total;
+        card = nc - free_total;
         if (n_roots == 0) break;
         if (phases >= max_phases) { status = -4 /*BM_ERR_ITER_LIMIT*/; break; }
         ++phases;
         // ---- BFS levels; sm.qn is the queue tail, sm.qbase the endpoint count
+        if (t == 0) { sm.qn = n_roots; sm.qbase = 0; }
+        __syncthreads();
         int qb = 0, qe = n_roots, lvl = L0, levels = 0, n_ep = 0;
         auto push_col = [&](int2 v) { p.queue[atomicAdd(&sm.qn, 1)] = v; };
         auto push_end = [&](int v) { p.endpoints[atomicAdd(&sm.qbase, 1)] = v; };
@@ -587,16 +650,17 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
             qe = tail;
             ++lvl;
         }
+        const int tail = sm.qn;
         levels_total += levels;
         eps_total += n_ep;
         if (status) break;
         if (n_ep == 0) break;  // no augmenting path: maximum (Berge)
-        // ---- Alternate (Algorithm 3) and the row half of FixMatching
+        // ---- Alternate (Algorithm 3)
         for (int i = t; i < n_ep; i += T) {
             int r = __ldcg(&p.endpoints[i]);
             int steps = 0;
             while (r != -1) {
-                if (++steps > levels + 2) { atomicCAS(&sm.ok, 0, -4); break; }
+                if (++steps > tail + 2) { atomicCAS(&sm.ok, 0, -4); break; }
                 const int c = __ldcg(&p.pred[r]);
                 if ((unsigned)c >= (unsigned)nc) { atomicCAS(&sm.ok, 0, -7); break; }
                 const int r2 = ld_volatile(&p.cmatch[c]);
@@ -608,16 +672,50 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
             }
         }
         __syncthreads();
-        for (int r = t; r < nr; r += T) {
-            const int m = __ldcg(&p.rmatch[r]);
-            if (m == -1) continue;
-            if (m < 0 || __ldcg(&p.cmatch[m]) != r) {
-                __stcg(&p.rmatch[r], -1);
-                cnt.fixes++;
-            }
-        }
-        __syncthreads();
         if (sm.ok != 0) { status = sm.ok; break; }
+        if (incremental) {
+            // columns inserted by this search go back to "unvisited" ...
+            for (int i = n_roots + t; i < tail; i += T) {
+                const int c = __ldcg(&p.queue[i]).x;
+                __stcg(&p.level[c], L0 - 1);
+                if (WR) __stcg(&p.root[c], -1);
+            }
+            // ... and the roots that are still unmatched stay roots (compacted in place:
+            // entry i moves to a position <= i, after every entry up to i has been read)
+            int kept = 0;
+            for (int base = 0; base < n_roots; base += T) {
+                const int i = base + t;
+                int c = -1, keep = 0;
+                if (i < n_roots) {
+                    c = __ldcg(&p.queue[i]).x;
+                    keep = __ldcg(&p.cmatch[c]) < 0;
+                    if (!keep) {
+                        __stcg(&p.level[c], L0 - 1);
+                        if (WR) __stcg(&p.root[c], -1);
+                    }
+                }
+                const int pos = block_exclusive_scan(keep, sm);
+                const int chunk = sm.total;
+                if (keep) p.queue[kept + pos] = make_int2(c, c);
+                kept += chunk;
+                __syncthreads();
+            }
+            n_roots = kept;
+            free_total = iso_free + kept;
+        } else {
+            // ---- row half of FixMatching, then InitBfsArray over every column
+            for (int r = t; r < nr; r += T) {
+                const int m = __ldcg(&p.rmatch[r]);
+                if (m == -1) continue;
+                if (m < 0 || __ldcg(&p.cmatch[m]) != r) {
+                    __stcg(&p.rmatch[r], -1);
+                    cnt.fixes++;
+                }
+            }
+            __syncthreads();
+            block_full_init<WR, NC>(p, sm, cnt, free_total, iso_free);
+            n_roots = sm.qn;
+        }
     }
     card_out = card;
     phases_out = phases + 1;

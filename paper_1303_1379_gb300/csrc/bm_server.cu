@@ -65,6 +65,7 @@ struct ServeParams {
     const SlotDesc* desc;
     SlotDone* done;
     unsigned long long* claimed;  // device memory: tickets claimed so far
+    int32_t* busy;                // device memory: blocks working on a request
     int32_t ring;
     int32_t mode, one_ep;
     int32_t pad;
@@ -103,17 +104,27 @@ __global__ void __launch_bounds__(1024, 1) k_serve(ServeParams sp) {
     for (;;) {
         __syncthreads();  // s_ticket / s_d of the previous round have been read
         if (threadIdx.x == 0) {
+            // Poll for work with exponential back-off.  A block leaves only when
+            // no block has been busy for idle_ns, so the workers stay together
+            // while any request runs and leave together when the server idles.
             long long t = -1;
-            for (int spin = 0; spin < 256 && t == -1; ++spin) {
+            unsigned sleep_ns = 128;
+            for (int spin = 0; spin < 64 && t == -1; ++spin) {
                 if (ld_relaxed_sys_s32(&sp.head->stop)) { t = -2; break; }
                 const long long pub = ld_acquire_sys_s64(&sp.head->published);
                 const unsigned long long c = *(volatile unsigned long long*)sp.claimed;
                 if ((long long)c < pub) {
-                    if (atomicCAS(sp.claimed, c, c + 1) == c) t = (long long)c;
+                    if (atomicCAS(sp.claimed, c, c + 1) == c) {
+                        t = (long long)c;
+                        atomicAdd(sp.busy, 1);
+                    }
                     continue;
                 }
-                if (bmd::globaltimer() - idle0 > (unsigned long long)sp.idle_ns) { t = -2; break; }
-                __nanosleep(256);
+                const unsigned long long now = bmd::globaltimer();
+                if (bmd::ld_volatile(sp.busy) > 0) idle0 = now;
+                if (now - idle0 > (unsigned long long)sp.idle_ns) { t = -2; break; }
+                __nanosleep(sleep_ns);
+                if (sleep_ns < 16384) sleep_ns <<= 1;
             }
             s_ticket = t;
             if (t >= 0) {
@@ -171,6 +182,8 @@ __global__ void __launch_bounds__(1024, 1) k_serve(ServeParams sp) {
             st_relaxed_sys_s32(&d->phases, phases);
             __threadfence_system();
             st_release_sys_s32(&d->done, (int)(t + 1));
+            atomicSub(sp.busy, 1);
+            idle0 = bmd::globaltimer();
         }
     }
 }
@@ -276,6 +289,7 @@ struct bm_server {
     SlotDone* done = nullptr;
     void* d_mapped = nullptr;  // device view
     unsigned long long* d_claimed = nullptr;
+    int32_t* d_busy = nullptr;
     cudaEvent_t worker_ev = nullptr;
     bool worker_launched = false;
     std::mutex mu;
@@ -303,6 +317,7 @@ void launch_workers(bm_server* s) {
     sp.desc = (const SlotDesc*)(dm + sizeof(MappedHead));
     sp.done = (SlotDone*)(dm + sizeof(MappedHead) + sizeof(SlotDesc) * (size_t)s->opt.ring_slots);
     sp.claimed = s->d_claimed;
+    sp.busy = s->d_busy;
     sp.ring = s->opt.ring_slots;
     sp.mode = s->opt.mode;
     sp.one_ep = 1;
@@ -441,7 +456,7 @@ void bm_server_default_options(bm_server_options* o) {
     o->mode = BM_APFB;
     o->bfs = BM_GPUBFS_WR;
     o->keep_results = 0;
-    o->idle_timeout_ns = 20000000;  // 20 ms
+    o->idle_timeout_ns = 50000000;  // 50 ms
     o->poll_interval_us = 5;
 }
 
@@ -492,8 +507,8 @@ int32_t bm_server_create(const bm_server_options* opt, bm_server** out) {
     s->desc = (SlotDesc*)((char*)s->mapped + sizeof(MappedHead));
     s->done = (SlotDone*)((char*)s->mapped + sizeof(MappedHead) + sizeof(SlotDesc) * (size_t)o.ring_slots);
     if (cudaHostGetDevicePointer(&s->d_mapped, s->mapped, 0) != cudaSuccess ||
-        cudaMalloc((void**)&s->d_claimed, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMemset(s->d_claimed, 0, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc((void**)&s->d_claimed, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(s->d_claimed, 0, 2 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->work_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->worker_ev, cudaEventDisableTiming) != cudaSuccess ||
@@ -501,6 +516,7 @@ int32_t bm_server_create(const bm_server_options* opt, bm_server** out) {
         (void)cudaGetLastError();
         return fail(BM_ERR_CUDA);
     }
+    s->d_busy = (int32_t*)(s->d_claimed + 1);
     s->ring_owner.assign((size_t)o.ring_slots, -1);
     s->running = true;
     s->sched = std::thread(scheduler_main, s);

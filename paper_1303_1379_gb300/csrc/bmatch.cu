@@ -212,17 +212,26 @@ __global__ void k_fill(int32_t* a, long long n, int v) {
 
 // Cheap matching: each unmatched column claims the first unmatched row of its
 // list by CAS.  A column stays unmatched only if all its rows were taken, so
-// the result is maximal.
+// the result is maximal.  The scan looks at 4 rows per step with their loads
+// in flight together (hub columns can pass many taken rows).
 __global__ void k_greedy(int nc, const int32_t* __restrict__ cp, const int32_t* __restrict__ ri,
                          int32_t* rm, int32_t* cm) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
         if (cm[c] != -1) continue;
         const int end = __ldg(&cp[c + 1]);
-        for (int e = __ldg(&cp[c]); e < end; ++e) {
-            const int r = __ldg(&ri[e]);
-            if (bmd::ld_volatile(&rm[r]) == -1 && atomicCAS(&rm[r], -1, c) == -1) {
-                cm[c] = r;
-                break;
+        bool done = false;
+        for (int e = __ldg(&cp[c]); e < end && !done; e += 4) {
+            int r[4], m[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) r[u] = e + u < end ? __ldg(&ri[e + u]) : -1;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) m[u] = r[u] >= 0 ? bmd::ld_volatile(&rm[r[u]]) : 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!done && m[u] == -1 && atomicCAS(&rm[r[u]], -1, c) == -1) {
+                    cm[c] = r[u];
+                    done = true;
+                }
             }
         }
     }
