@@ -136,7 +136,8 @@ BM_API const char *bm_status_string(int32_t status);
  *   stream: cudaStream_t to issue all work on (NULL = the legacy default stream).
  *   opt: NULL for defaults.
  * The context owns its workspace (matching, levels, roots, predecessors, one
- * (column, root) queue, the endpoint list: about 4*(5*n_cols + 3*n_rows) bytes),
+ * (column, root) queue and a second one for the next phase's roots, the
+ * endpoint list: about 4*(7*n_cols + 3*n_rows) bytes),
  * allocated here.  The matching starts empty.
  */
 BM_API int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *col_ptr,

@@ -56,6 +56,7 @@ struct alignas(128) Ctl {
     int32_t pad_rel[30];
     int32_t qcnt[3];           // columns appended during a step (queue positions)
     int32_t ecnt[3];           // init: unmatched columns counted during a step
+    int32_t icnt[3];           // init: unmatched columns without rows counted during a step
     int32_t tcnt[3];           // tiles handed out during a step
     int32_t ep_phase;          // endpoints appended in the current phase (positions)
     int32_t err;               // first error code (0 = none)
@@ -64,7 +65,7 @@ struct alignas(128) Ctl {
     int32_t initial_card;
     int32_t phases;
     int32_t n_endpoints_last;  // endpoints of the last BFS (inspection)
-    int32_t pad1[14];
+    int32_t pad1[11];
     long long levels;
     long long max_levels;
     long long cols_expanded;
@@ -87,6 +88,7 @@ struct Params {
     int32_t* root;       // root array of GPUBFS-WR
     int32_t* pred;       // predecessor array
     int2* queue;         // (column, root) of the current phase, level by level
+    int2* queue2;        // second queue buffer: roots of the next phase (nullable)
     int32_t* endpoints;  // rows claimed as path ends in the current phase
     Ctl* ctl;
     int32_t mode;        // 0 APFB, 1 APsB
@@ -108,7 +110,7 @@ struct Smem {
     int total;  // edges of the current tile
     int npush;  // columns this block appended during the current step
     int has_ep; // this block appended an endpoint during the current step
-    int bc_a, bc_b, bc_c, ok;  // barrier broadcast
+    int bc_a, bc_b, bc_c, bc_d, ok;  // barrier broadcast
     int wsum[32];
     int off[MAX_BLOCK];  // exclusive prefix of the tile's degrees
     int beg[MAX_BLOCK];  // first edge of each tile column
@@ -162,15 +164,15 @@ __device__ __forceinline__ void push(T* buf, int base, int32_t* slot, T v) {
 }
 
 // Appends a (column, root) entry to the block's buffer (global fallback when it is full).
-__device__ __forceinline__ void push_block(const Params& p, Smem& sm, int qbase, int slot, int2 v) {
+__device__ __forceinline__ void push_block(const Params& p, int2* q, Smem& sm, int qbase, int slot, int2 v) {
     const int pos = atomicAdd(&sm.qn, 1);
     if (pos < QBUF) sm.qbuf[pos] = v;
-    else push(p.queue, qbase, &p.ctl->qcnt[slot], v);
+    else push(q, qbase, &p.ctl->qcnt[slot], v);
 }
 
 // Writes the block's buffer to queue[qbase + ...] with one global atomic and
 // adds this tile's appends to sm.npush.  Called by all threads of the block.
-__device__ __forceinline__ void flush_block(const Params& p, Smem& sm, int qbase, int slot) {
+__device__ __forceinline__ void flush_block(const Params& p, int2* q, Smem& sm, int qbase, int slot) {
     __syncthreads();
     const int n = min(sm.qn, QBUF);
     if (threadIdx.x == 0) {
@@ -180,7 +182,7 @@ __device__ __forceinline__ void flush_block(const Params& p, Smem& sm, int qbase
     __syncthreads();
     if (n > 0) {
         const int b = qbase + sm.qbase;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) p.queue[b + k] = sm.qbuf[k];
+        for (int k = threadIdx.x; k < n; k += blockDim.x) q[b + k] = sm.qbuf[k];
     }
     if (threadIdx.x == 0) sm.qn = 0;  // the next write to qbuf/qn is behind a __syncthreads
 }
@@ -234,13 +236,13 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
 // others poll with relaxed loads (one acquire fence after the wait).  So
 // every block learns the level's totals without reading a counter after the
 // barrier: sm.bc_a = appended columns, sm.bc_b = blocks that found endpoints.
-// If extra_ptr is given, thread 0 also reads it after the barrier into
-// sm.bc_c.  Returns false (in every thread of the block) when the wait ran
+// If extra_ptr / extra_ptr2 are given, thread 0 also reads them after the
+// barrier into sm.bc_c / sm.bc_d.  Returns false (in every thread of the block) when the wait ran
 // out of time, the launch deadline passed or a block recorded an error; the
 // caller then leaves the kernel.
 static __device__ __noinline__ bool grid_sync(Ctl* ctl, int& bid, long long wait_ns,
                                               unsigned long long deadline, Smem& sm,
-                                              const int32_t* extra_ptr) {
+                                              const int32_t* extra_ptr, const int32_t* extra_ptr2 = nullptr) {
     __syncthreads();
     const int b = bid++;
     if (threadIdx.x == 0) {
@@ -272,6 +274,7 @@ static __device__ __noinline__ bool grid_sync(Ctl* ctl, int& bid, long long wait
         sm.bc_a = (int)(rel & 0xFFFFFFFFull);
         sm.bc_b = (int)((rel >> 32) & 0x7FFull);
         if (extra_ptr) sm.bc_c = ld_volatile(extra_ptr);
+        if (extra_ptr2) sm.bc_d = ld_volatile(extra_ptr2);
         sm.npush = 0;
         sm.has_ep = 0;
         sm.ok = ok;
@@ -293,9 +296,9 @@ struct Counters {
 // ecnt[slot].  Before that, the column half of FixMatching: a column whose
 // row does not point back is unmatched (the row half runs after Alternate).
 template <bool WR>
-__device__ __forceinline__ void step_init(const Params& p, int slot, Counters& cnt, Smem& sm) {
+__device__ __forceinline__ void step_init(const Params& p, int2* q, int slot, Counters& cnt, Smem& sm) {
     const int nc = p.nc;
-    int nfree = 0;
+    int nfree = 0, niso = 0;
     for (int base = blockIdx.x * blockDim.x; base < nc; base += gridDim.x * blockDim.x) {  // block-uniform
         const int c = base + threadIdx.x;
         if (c < nc) {
@@ -310,14 +313,49 @@ __device__ __forceinline__ void step_init(const Params& p, int slot, Counters& c
             if (WR) __stcg(&p.root[c], is_free ? c : -1);
             if (is_free) {
                 ++nfree;
-                if (__ldg(&p.col_ptr[c + 1]) > __ldg(&p.col_ptr[c])) push_block(p, sm, 0, slot, make_int2(c, c));
+                if (__ldg(&p.col_ptr[c + 1]) > __ldg(&p.col_ptr[c])) push_block(p, q, sm, 0, slot, make_int2(c, c));
+                else ++niso;
             }
         }
-        flush_block(p, sm, 0, slot);
+        flush_block(p, q, sm, 0, slot);
     }
 #pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) nfree += __shfl_down_sync(FULL, nfree, s);
+    for (int s = 16; s >= 1; s >>= 1) {
+        nfree += __shfl_down_sync(FULL, nfree, s);
+        niso += __shfl_down_sync(FULL, niso, s);
+    }
     if ((threadIdx.x & 31) == 0 && nfree) atomicAdd(&p.ctl->ecnt[slot], nfree);
+    if ((threadIdx.x & 31) == 0 && niso) atomicAdd(&p.ctl->icnt[slot], niso);
+}
+
+// Between phases in the one-endpoint GPUBFS-WR mode (where Alternate's walks
+// cannot meet, so FixMatching has nothing to repair and the columns not
+// touched by the search keep their InitBfsArray values): the columns the
+// search inserted go back to "unvisited" and the roots that are still
+// unmatched are appended to the other queue buffer as the next phase's roots.
+template <bool WR>
+__device__ __forceinline__ void step_next_roots(const Params& p, const int2* q, int n_roots, int tail,
+                                                int2* q_next, int slot, Smem& sm) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthr = gridDim.x * blockDim.x;
+    for (int i = n_roots + tid; i < tail; i += nthr) {
+        const int c = __ldcg(&q[i]).x;
+        __stcg(&p.level[c], L0 - 1);
+        if (WR) __stcg(&p.root[c], -1);
+    }
+    for (int base = blockIdx.x * blockDim.x; base < n_roots; base += gridDim.x * blockDim.x) {  // block-uniform
+        const int i = base + threadIdx.x;
+        if (i < n_roots) {
+            const int c = __ldcg(&q[i]).x;
+            if (__ldcg(&p.cmatch[c]) < 0) {
+                push_block(p, q_next, sm, 0, slot, make_int2(c, c));
+            } else {
+                __stcg(&p.level[c], L0 - 1);
+                if (WR) __stcg(&p.root[c], -1);
+            }
+        }
+        flush_block(p, q_next, sm, 0, slot);
+    }
 }
 
 // ------------------------------------------------------------------ BFS level
@@ -331,13 +369,13 @@ __device__ __forceinline__ void step_init(const Params& p, int slot, Counters& c
 // sm.col = -1 and its edges are skipped.  If tile_ctr is given, thread 0 also
 // takes the next tile index from it (into sm.tile).  Ends with __syncthreads.
 template <bool WR, bool NC = true>
-__device__ __forceinline__ void tile_load(const Params& p, int qb, int q, int first, int tw, Smem& sm,
-                                          Counters& cnt, int32_t* tile_ctr) {
+__device__ __forceinline__ void tile_load(const Params& p, const int2* queue, int qb, int q, int first, int tw,
+                                          Smem& sm, Counters& cnt, int32_t* tile_ctr) {
     const int t = threadIdx.x;
     const int i = first + t;
     int c = -1, beg = 0, deg = 0, myroot = -1, rlev = L0;
     if (t < tw && i < q) {
-        const int2 ent = __ldcg(&p.queue[qb + i]);
+        const int2 ent = __ldcg(&queue[qb + i]);
         c = ent.x;
         myroot = ent.y;
         beg = ld_csr<NC>(&p.col_ptr[c]);
@@ -433,7 +471,7 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
 // block (the deep, narrow levels of long augmenting paths) take their tile
 // from blockIdx.x alone and claim columns by CAS without a test load.
 template <bool WR>
-__device__ __forceinline__ void step_expand(const Params& p, int qb, int qe, int lvl, int slot,
+__device__ __forceinline__ void step_expand(const Params& p, int2* queue, int qb, int qe, int lvl, int slot,
                                             Counters& cnt, Smem& sm) {
     const int q = qe - qb;
     // tile width: spread small frontiers over many blocks, never above blockDim
@@ -443,13 +481,13 @@ __device__ __forceinline__ void step_expand(const Params& p, int qb, int qe, int
     if (tw < 32) tw = 32;
     const int ntiles = (q + tw - 1) / tw;
     const bool narrow = ntiles <= (int)gridDim.x;
-    auto push_col = [&](int2 v) { push_block(p, sm, qe, slot, v); };
+    auto push_col = [&](int2 v) { push_block(p, queue, sm, qe, slot, v); };
     auto push_end = [&](int v) { push(p.endpoints, 0, &p.ctl->ep_phase, v); };
     for (int tile = blockIdx.x; tile < ntiles;) {  // block-uniform
-        tile_load<WR>(p, qb, q, tile * tw, tw, sm, cnt, narrow ? nullptr : &p.ctl->tcnt[slot]);
+        tile_load<WR>(p, queue, qb, q, tile * tw, tw, sm, cnt, narrow ? nullptr : &p.ctl->tcnt[slot]);
         const int next_tile = narrow ? ntiles : sm.tile;
         tile_edges<WR>(p, tw, lvl, narrow, sm, cnt, push_col, push_end);
-        flush_block(p, sm, qe, slot);
+        flush_block(p, queue, sm, qe, slot);
         tile = next_tile;
     }
 }
@@ -634,7 +672,7 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
         for (;;) {
             const int q = qe - qb;
             for (int first = 0; first < q; first += T) {
-                tile_load<WR, NC>(p, qb, q, first, T, sm, cnt, nullptr);
+                tile_load<WR, NC>(p, p.queue, qb, q, first, T, sm, cnt, nullptr);
                 tile_edges<WR, decltype(push_col), decltype(push_end), NC>(p, T, lvl, q <= T, sm, cnt,
                                                                            push_col, push_end);
                 __syncthreads();  // sm.off/beg/col/root are reused by the next tile

@@ -44,29 +44,38 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
     const unsigned long long t_start = globaltimer();
     const unsigned long long deadline = t_start + (unsigned long long)p.total_ns;
     const bool leader = (blockIdx.x == 0 && threadIdx.x == 0);
+    // one-endpoint GPUBFS-WR: no FixMatching passes, roots carried to the next phase
+    const bool incr = WR && p.one_ep && p.queue2 != nullptr && !p.bfs_only;
+    int2* qcur = p.queue;
+    int2* qnext = p.queue2;
     Counters cnt{0, 0, 0, 0, 0};
     int step = 0;
     int phases = 0;
     int card = 0;
     int status = 0;
+    int n_roots = 0;
+    int iso_free = 0;
     long long levels_total = 0, levels_max = 0, eps_total = 0, ins_total = 0;
     if (ld_volatile(&ctl->err) != 0) goto out;  // input validation failed before launch
-
-    for (;;) {
+    {
         // ---- InitBfsArray (+ column half of FixMatching)
-        int s = step++;
+        const int s = step++;
         if (leader) {
             ctl->qcnt[(s + 1) % 3] = 0;
             ctl->ecnt[(s + 1) % 3] = 0;
+            ctl->icnt[(s + 1) % 3] = 0;
             ctl->tcnt[(s + 1) % 3] = 0;
             ctl->ep_phase = 0;
         }
-        step_init<WR>(p, s % 3, cnt, sm);
-        if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, &ctl->ecnt[s % 3])) goto out;
-        const int n_roots = sm.bc_a;  // unmatched columns with rows: the first queue segment
-        card = p.nc - sm.bc_c;        // all unmatched columns
-        if (leader && phases == 0) ctl->initial_card = card;
-        if (n_roots == 0) break;  // every column matched
+        step_init<WR>(p, qcur, s % 3, cnt, sm);
+        if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, &ctl->ecnt[s % 3], &ctl->icnt[s % 3])) goto out;
+        n_roots = sm.bc_a;       // unmatched columns with rows: the first queue segment
+        card = p.nc - sm.bc_c;   // all unmatched columns
+        iso_free = sm.bc_d;      // unmatched columns without rows (never matchable)
+        if (leader) ctl->initial_card = card;
+    }
+    for (;;) {
+        if (n_roots == 0) break;  // no column left to search from
         if (phases >= p.max_phases) {
             status = p.phase_limit_is_error ? -4 /*BM_ERR_ITER_LIMIT*/ : 1 /*BM_INCOMPLETE*/;
             break;
@@ -74,11 +83,11 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
         ++phases;
 
         // ---- BFS, level by level (Algorithm 1 inner loop)
-        int qb = 0, qe = n_roots, lvl = L0, levels = 0, first_ep = 0, last_ep = 0;
+        int qb = 0, qe = n_roots, lvl = L0, levels = 0, first_ep = 0, last_ep = 0, tail = n_roots;
         for (;;) {
-            int s2 = step++;
-            if (leader) { ctl->qcnt[(s2 + 1) % 3] = 0; ctl->ecnt[(s2 + 1) % 3] = 0; ctl->tcnt[(s2 + 1) % 3] = 0; }
-            step_expand<WR>(p, qb, qe, lvl, s2 % 3, cnt, sm);
+            const int s2 = step++;
+            if (leader) { ctl->qcnt[(s2 + 1) % 3] = 0; ctl->ecnt[(s2 + 1) % 3] = 0; ctl->icnt[(s2 + 1) % 3] = 0; ctl->tcnt[(s2 + 1) % 3] = 0; }
+            step_expand<WR>(p, qcur, qb, qe, lvl, s2 % 3, cnt, sm);
             if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
             const int nq = sm.bc_a;           // columns inserted at this level
             const bool found = sm.bc_b > 0;   // some block claimed an endpoint
@@ -88,6 +97,7 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
                 last_ep = levels;
             }
             ins_total += nq;
+            tail = qe + nq;
             if (nq == 0) break;              // no vertex inserted
             if (p.mode == 1 && found) break;  // APsB: stop at the first level with a path
             qb = qe;
@@ -118,11 +128,37 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
         }
         if (n_ep == 0) break;  // no augmenting path: the matching is maximum (Berge)
 
-        // ---- Alternate, then the row half of FixMatching
-        step_alternate(p, n_ep, levels + 2, cnt);
+        // ---- Alternate (Algorithm 3); the walk is at most as long as the forest
+        step_alternate(p, n_ep, tail + 2, cnt);
         if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
-        step_fix_rows(p, cnt);
-        if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
+        if (incr) {
+            // ---- next phase's roots: the unmatched ones among this phase's roots
+            const int s3 = step++;
+            if (leader) {
+                ctl->qcnt[(s3 + 1) % 3] = 0; ctl->ecnt[(s3 + 1) % 3] = 0; ctl->icnt[(s3 + 1) % 3] = 0; ctl->tcnt[(s3 + 1) % 3] = 0;
+                ctl->ep_phase = 0;
+            }
+            step_next_roots<WR>(p, qcur, n_roots, tail, qnext, s3 % 3, sm);
+            if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
+            n_roots = sm.bc_a;
+            card = p.nc - (iso_free + n_roots);
+            int2* t = qcur;
+            qcur = qnext;
+            qnext = t;
+        } else {
+            // ---- row half of FixMatching, then InitBfsArray (+ column half)
+            step_fix_rows(p, cnt);
+            if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
+            const int s = step++;
+            if (leader) {
+                ctl->qcnt[(s + 1) % 3] = 0; ctl->ecnt[(s + 1) % 3] = 0; ctl->icnt[(s + 1) % 3] = 0; ctl->tcnt[(s + 1) % 3] = 0;
+                ctl->ep_phase = 0;
+            }
+            step_init<WR>(p, qcur, s % 3, cnt, sm);
+            if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, &ctl->ecnt[s % 3])) goto out;
+            n_roots = sm.bc_a;
+            card = p.nc - sm.bc_c;
+        }
     }
 out:
     flush_counters(p, cnt);
@@ -146,7 +182,7 @@ __global__ void __launch_bounds__(1024) k_init(Params p, int slot) {
     if (threadIdx.x == 0) { sm.qn = 0; sm.npush = 0; sm.has_ep = 0; }
     __syncthreads();
     Counters cnt{0, 0, 0, 0, 0};
-    bmd::step_init<WR>(p, slot, cnt, sm);
+    bmd::step_init<WR>(p, p.queue, slot, cnt, sm);
     bmd::flush_counters(p, cnt);
 }
 template <bool WR>
@@ -155,7 +191,7 @@ __global__ void __launch_bounds__(1024) k_expand(Params p, int qb, int qe, int l
     if (threadIdx.x == 0) { sm.qn = 0; sm.npush = 0; sm.has_ep = 0; }
     __syncthreads();
     Counters cnt{0, 0, 0, 0, 0};
-    bmd::step_expand<WR>(p, qb, qe, lvl, slot, cnt, sm);
+    bmd::step_expand<WR>(p, p.queue, qb, qe, lvl, slot, cnt, sm);
     bmd::flush_counters(p, cnt);
 }
 __global__ void __launch_bounds__(1024) k_alternate(Params p, int n_ep, int cap) {
@@ -265,6 +301,7 @@ struct bm_ctx {
     int32_t* root = nullptr;
     int32_t* pred = nullptr;
     int2* queue = nullptr;
+    int2* queue2 = nullptr;  // roots of the next phase (one-endpoint GPUBFS-WR)
     int32_t* endpoints = nullptr;
     int32_t* profile = nullptr;  // kProfileCap phases x 4
     Ctl* ctl = nullptr;
@@ -337,6 +374,7 @@ Params make_params(bm_ctx* ctx, bool bfs_only) {
     p.root = ctx->root;
     p.pred = ctx->pred;
     p.queue = ctx->queue;
+    p.queue2 = ctx->queue2;
     p.endpoints = ctx->endpoints;
     p.ctl = ctx->ctl;
     p.mode = ctx->opt.mode;
@@ -588,7 +626,8 @@ int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* co
     size_t off_rt = off_lv + al(4 * nc1);
     size_t off_pd = off_rt + al(4 * nc1);
     size_t off_q = off_pd + al(4 * nr1);
-    size_t off_ep = off_q + al(8 * nc1);
+    size_t off_q2 = off_q + al(8 * nc1);
+    size_t off_ep = off_q2 + al(8 * nc1);
     size_t off_pf = off_ep + al(4 * nr1);
     size_t off_cp = off_pf + al(4 * 4 * (size_t)kProfileCap);
     size_t total = off_cp;
@@ -617,6 +656,7 @@ int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* co
     ctx->root = (int32_t*)(a + off_rt);
     ctx->pred = (int32_t*)(a + off_pd);
     ctx->queue = (int2*)(a + off_q);
+    ctx->queue2 = (int2*)(a + off_q2);
     ctx->endpoints = (int32_t*)(a + off_ep);
     ctx->profile = (int32_t*)(a + off_pf);
     if (own) {
