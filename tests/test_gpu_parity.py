@@ -339,3 +339,5 @@ def test_phase_profile_matches_counters(c1, driver):
     assert np.all((ends > 0) == (first > 0))
     assert np.all(first <= last) and np.all(last <= levels)
     assert ends[-1] == 0  # the last searching phase found no path
+    assert st["final_card"] == golden_workloads()["uniform10k"]["max"]
+
