@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-distinct", type=int, default=48)
+    ap.add_argument("--variant-table", action="store_true",
+                    help="print the variant matrix (Table 1 / Fig. 2 quantities) instead")
+    ap.add_argument("--table-workloads", default="rmat21,rmat21-rcp,stencil2000,stencil2000-rcp")
+    ap.add_argument("--table-reps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -266,11 +270,18 @@ BATCH_WORKLOAD = ("4,096 uniform random bipartite graphs, rows log-uniform in [1
 
 def bench_batched(args, torch, bmatch, stream, flush):
     """Batched graphs/s (one persistent launch, geometry from the autotuner)
-    against the single-graph path called once per graph on the same stream."""
-    from paper_1303_1379_gb300 import synth
+    against the single-graph path called once per graph on the same stream.
+    With N ranks each rank matches its largest-first share of the graphs and
+    the slowest rank's time counts."""
+    import numpy as np
+    from paper_1303_1379_gb300 import shard, synth
     t_gen = time.perf_counter()
     b = synth.batch_graphs(4096, seed=3)
     t_gen = time.perf_counter() - t_gen
+    rank, world, _ = dist_env()
+    G_all = b.n_graphs
+    if world > 1:  # whole graphs dealt to ranks largest first; no collective on the data path
+        b = b.subset(shard.lpt_partition(np.diff(b.edge_off), world)[rank])
     G = b.n_graphs
     R, C, E = int(b.row_off[-1]), int(b.col_off[-1]), int(b.edge_off[-1])
     bb = bmatch.Batch.from_synth(b, stream=stream.cuda_stream)
@@ -323,6 +334,11 @@ def bench_batched(args, torch, bmatch, stream, flush):
         m.close()
     one_ms = min(one)
     bb.close()
+    if world > 1:
+        batch_ms, one_ms = shard.max_over_ranks([batch_ms, one_ms], device=dev)
+        E = int(shard.sum_over_ranks([E], device=dev)[0])
+        ok = shard.sum_over_ranks([0 if ok else 1], device=dev)[0] == 0
+        G = G_all
     return {
         "workload": BATCH_WORKLOAD, "graphs": G, "rows": R, "cols": C, "edges": E,
         "generate_s": round(t_gen, 2),
@@ -342,18 +358,8 @@ def batched_cpu_baseline(b, batch_cards):
     import numpy as np
     import oracle
     rng = np.random.default_rng(3)
-    idx = np.sort(rng.choice(b.n_graphs, size=256, replace=False))
-    from paper_1303_1379_gb300.synth import Batch
-    nr, nc = b.n_rows[idx], b.n_cols[idx]
-    ro = np.zeros(len(idx) + 1, np.int64); np.cumsum(nr, out=ro[1:])
-    co = np.zeros(len(idx) + 1, np.int64); np.cumsum(nc, out=co[1:])
-    cps, ris, eo = [], [], [0]
-    for k in idx:
-        g = b.graph(int(k))
-        cps.append(g.col_ptr)
-        ris.append(g.row_idx)
-        eo.append(eo[-1] + g.nnz)
-    sub = Batch(nr, nc, ro, co, np.array(eo, np.int64), np.concatenate(cps), np.concatenate(ris))
+    idx = np.sort(rng.choice(b.n_graphs, size=min(256, b.n_graphs), replace=False))
+    sub = b.subset(idx)
     t = time.perf_counter()
     _, _, cards = oracle.hk_batch(sub, greedy_first=True)
     dt = time.perf_counter() - t
@@ -642,8 +648,70 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ variant table
+VARIANTS = [
+    ("APFB", "GPUBFS-WR", "one", "persistent", dict(mode=0, bfs=1, wr_one_endpoint=1, driver=0)),
+    ("APFB", "GPUBFS-WR", "many", "persistent", dict(mode=0, bfs=1, wr_one_endpoint=0, driver=0)),
+    ("APFB", "GPUBFS", "-", "persistent", dict(mode=0, bfs=0, driver=0)),
+    ("APsB", "GPUBFS-WR", "one", "persistent", dict(mode=1, bfs=1, wr_one_endpoint=1, driver=0)),
+    ("APsB", "GPUBFS-WR", "many", "persistent", dict(mode=1, bfs=1, wr_one_endpoint=0, driver=0)),
+    ("APsB", "GPUBFS", "-", "persistent", dict(mode=1, bfs=0, driver=0)),
+    ("APFB", "GPUBFS-WR", "one", "host loop", dict(mode=0, bfs=1, wr_one_endpoint=1, driver=1)),
+    ("APFB", "GPUBFS", "-", "host loop", dict(mode=0, bfs=0, driver=1)),
+]
+
+
+def run_variant_table(args):
+    """The paper's variant matrix (Table 1: APFB / APsB x GPUBFS / GPUBFS-WR x
+    thread mapping) on this build's workloads, original and randomly permuted
+    (Section 4's RCP sets), with Fig. 2's quantities (phases, BFS levels per
+    phase).  One JSON line per (workload, variant)."""
+    import torch
+    from paper_1303_1379_gb300 import bmatch
+    names = args.table_workloads.split(",")
+    for name in names:
+        g = load_workload(name)
+        cp = torch.from_numpy(g.col_ptr).cuda()
+        ri = torch.from_numpy(g.row_idx).cuda()
+        base = bmatch.Matcher(g.n_rows, g.n_cols, g.nnz, cp, ri)
+        if not name.startswith("uniform10k"):
+            base.greedy()
+        rm0 = torch.empty(g.n_rows, dtype=torch.int32, device="cuda")
+        cm0 = torch.empty(g.n_cols, dtype=torch.int32, device="cuda")
+        base.get_matching(rm0, cm0)
+        base.close()
+        want = golden_max(name)
+        for mode, bfs, eps, drv, opt in VARIANTS:
+            if drv == "host loop" and name.startswith("stencil") and bfs == "GPUBFS":
+                continue  # ~200k host round trips; the persistent rows show the same search
+            m = bmatch.Matcher(g.n_rows, g.n_cols, g.nnz, cp, ri, **opt)
+            times = []
+            for _ in range(1 if name.startswith("stencil") else args.table_reps):
+                m.set_matching(rm0, cm0)
+                torch.cuda.synchronize()
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                r = m.match()
+                z.record()
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(z))
+            lv, ep, _, _ = m.phase_profile()
+            m.close()
+            st = r.stats
+            print(json.dumps({
+                "workload": name, "mode": mode, "bfs": bfs, "endpoints_per_root": eps, "driver": drv,
+                "ms": statistics.median(times), "max_matching": r.card,
+                "correct": (want is None or r.card == want), "phases": st["phases"],
+                "levels": st["levels"], "max_levels_in_phase": st["max_levels_in_phase"],
+                "edges_scanned": st["edges_scanned"], "levels_per_phase": lv.tolist()[:64],
+                "endpoints_per_phase": ep.tolist()[:64]}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.variant_table:
+        return run_variant_table(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -171,6 +171,24 @@ class Batch:
     def n_graphs(self) -> int:
         return int(self.n_rows.shape[0])
 
+    def subset(self, idx) -> "Batch":
+        """The graphs idx (in that order) as a batch of their own."""
+        idx = np.asarray(idx, dtype=np.int64)
+        nr, nc = self.n_rows[idx], self.n_cols[idx]
+        ro = np.zeros(len(idx) + 1, np.int64)
+        np.cumsum(nr, out=ro[1:])
+        co = np.zeros(len(idx) + 1, np.int64)
+        np.cumsum(nc, out=co[1:])
+        cps, ris, eo = [], [], [0]
+        for k in idx:
+            g = self.graph(int(k))
+            cps.append(g.col_ptr)
+            ris.append(g.row_idx)
+            eo.append(eo[-1] + g.nnz)
+        return Batch(nr.copy(), nc.copy(), ro, co, np.array(eo, np.int64),
+                     np.concatenate(cps) if cps else np.zeros(0, np.int32),
+                     np.concatenate(ris) if ris else np.zeros(0, np.int32))
+
     def graph(self, k: int) -> Graph:
         cp = self.col_ptr[self.col_off[k] + k: self.col_off[k + 1] + k + 1]
         ri = self.row_idx[self.edge_off[k]: self.edge_off[k + 1]]
