@@ -283,8 +283,8 @@ static __device__ __noinline__ bool grid_sync(Ctl* ctl, int& bid, long long wait
     return sm.ok != 0;
 }
 
-struct Counters {
-    long long cols, edges, fixes, em, alt;
+struct Counters {  // per-thread, flushed once per launch (32 bits: a thread's share stays far below 2^32)
+    unsigned cols, edges, fixes, em, alt;
 };
 
 // ------------------------------------------------------------------ InitBfsArray
@@ -338,24 +338,40 @@ __device__ __forceinline__ void step_next_roots(const Params& p, const int2* q, 
                                                 int2* q_next, int slot, Smem& sm) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthr = gridDim.x * blockDim.x;
-    for (int i = n_roots + tid; i < tail; i += nthr) {
-        const int c = __ldcg(&q[i]).x;
-        __stcg(&p.level[c], L0 - 1);
-        if (WR) __stcg(&p.root[c], -1);
+    // 4 entries per thread per pass, their loads in flight together
+    for (int i0 = n_roots + tid; i0 < tail; i0 += 4 * nthr) {
+        int c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = i0 + u * nthr < tail ? __ldcg(&q[i0 + u * nthr]).x : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (c[u] < 0) continue;
+            __stcg(&p.level[c[u]], L0 - 1);
+            if (WR) __stcg(&p.root[c[u]], -1);
+        }
     }
-    for (int base = blockIdx.x * blockDim.x; base < n_roots; base += gridDim.x * blockDim.x) {  // block-uniform
-        const int i = base + threadIdx.x;
-        if (i < n_roots) {
-            const int c = __ldcg(&q[i]).x;
-            if (__ldcg(&p.cmatch[c]) < 0) {
-                push_block(p, q_next, sm, 0, slot, make_int2(c, c));
+    const int T = blockDim.x;
+    for (int base = blockIdx.x * T * 4; base < n_roots; base += gridDim.x * T * 4) {  // block-uniform
+        int c[4], m[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = base + u * T + threadIdx.x;
+            c[u] = i < n_roots ? __ldcg(&q[i]).x : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) m[u] = c[u] >= 0 ? __ldcg(&p.cmatch[c[u]]) : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (c[u] < 0) continue;
+            if (m[u] < 0) {
+                push_block(p, q_next, sm, 0, slot, make_int2(c[u], c[u]));
             } else {
-                __stcg(&p.level[c], L0 - 1);
-                if (WR) __stcg(&p.root[c], -1);
+                __stcg(&p.level[c[u]], L0 - 1);
+                if (WR) __stcg(&p.root[c[u]], -1);
             }
         }
-        flush_block(p, q_next, sm, 0, slot);
     }
+    flush_block(p, q_next, sm, 0, slot);  // a full buffer spills to global appends meanwhile
 }
 
 // ------------------------------------------------------------------ BFS level
@@ -793,7 +809,7 @@ __device__ bool block_check_csr(int nr, int nc, long long nnz, const int32_t* cp
 
 __device__ __forceinline__ void flush_counters(const Params& p, Counters& cnt) {
     // one atomic per warp
-    long long a = cnt.cols, b = cnt.edges, f = cnt.fixes, m = cnt.em, t = cnt.alt;
+    unsigned long long a = cnt.cols, b = cnt.edges, f = cnt.fixes, m = cnt.em, t = cnt.alt;
 #pragma unroll
     for (int s = 16; s >= 1; s >>= 1) {
         a += __shfl_down_sync(FULL, a, s);
