@@ -49,11 +49,9 @@ constexpr int ILP = 4;      // edges per thread in flight
 // after the barrier that ended step s - 2).
 struct alignas(128) Ctl {
     // grid barrier: arrival words rotate over barriers b % 3; each arrival adds
-    // 1 + (block has endpoints) << 11 + (block's appended columns) << 22
+    // 1 + (block has endpoints) << 11 + (block's appended columns) << 22, and
+    // the barrier is complete when the low 11 bits reach gridDim.x
     unsigned long long arrive[3][16];
-    // release word: (barrier id + 1) << 43 | blocks with endpoints << 32 | appended columns
-    unsigned long long release;
-    int32_t pad_rel[30];
     int32_t qcnt[3];           // columns appended during a step (queue positions)
     int32_t ecnt[3];           // init: unmatched columns counted during a step
     int32_t icnt[3];           // init: unmatched columns without rows counted during a step
@@ -133,9 +131,6 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -214,28 +209,25 @@ __device__ __forceinline__ int block_exclusive_scan(int v, Smem& sm) {
     return (warp > 0 ? sm.wsum[warp - 1] : 0) + incl - v;
 }
 
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ unsigned long long atom_add_acq_rel_u64(unsigned long long* p, unsigned long long v) {
-    unsigned long long r;
-    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(v) : "memory");
-    return r;
+__device__ __forceinline__ void red_add_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // ------------------------------------------------------------------ grid barrier
-// All blocks of a cooperative launch.  Block b of the grid adds one arrival,
-// a flag (sm.has_ep) and its appended-column count (sm.npush) to the arrival
-// word of this barrier with one acquire-release atomic; the last arriver
-// publishes the sums with the barrier id in one release store, which the
-// others poll with relaxed loads (one acquire fence after the wait).  So
-// every block learns the level's totals without reading a counter after the
-// barrier: sm.bc_a = appended columns, sm.bc_b = blocks that found endpoints.
+// All blocks of a cooperative launch.  Thread 0 of every block adds one
+// arrival, a flag (sm.has_ep) and its appended-column count (sm.npush) to the
+// arrival word of this barrier with one release reduction (no return value,
+// so the block does not wait for the atomic), then polls that same word with
+// acquire loads until its arrival count reaches gridDim.x.  The completed
+// word carries the level's totals, so every block learns them without a
+// separate release store or a counter read: sm.bc_a = appended columns,
+// sm.bc_b = blocks that found endpoints.  Words rotate over b % 3; block 0
+// clears word (b + 2) % 3 once barrier b is complete (every block has then
+// left barrier b - 1, the last user of that word, and none can reach barrier
+// b + 2 before block 0 has arrived at b + 1, after the clear).
 // If extra_ptr / extra_ptr2 are given, thread 0 also reads them after the
 // barrier into sm.bc_c / sm.bc_d.  Returns false (in every thread of the block) when the wait ran
 // out of time, the launch deadline passed or a block recorded an error; the
@@ -249,30 +241,23 @@ static __device__ __noinline__ bool grid_sync(Ctl* ctl, int& bid, long long wait
         int ok = 1;
         const unsigned long long inc =
             1ull + ((unsigned long long)(sm.has_ep ? 1 : 0) << 11) + ((unsigned long long)sm.npush << 22);
-        const unsigned long long prev = atom_add_acq_rel_u64(&ctl->arrive[b % 3][0], inc);
-        const unsigned long long want = (unsigned long long)((b + 1) & 0x1FFFFF);
-        unsigned long long rel;
-        if ((prev & 0x7FFull) + 1 == gridDim.x) {
-            const unsigned long long tot = prev + inc;
-            st_relaxed_u64(&ctl->arrive[(b + 2) % 3][0], 0ull);  // barrier b + 2's word, idle since b - 1
-            rel = (want << 43) | (((tot >> 11) & 0x7FFull) << 32) | ((tot >> 22) & 0xFFFFFFFFull);
-            st_release_u64(&ctl->release, rel);
-        } else {
-            unsigned long long t_end = globaltimer() + (unsigned long long)wait_ns;
-            if (t_end > deadline) t_end = deadline;
-            unsigned spins = 0;
-            for (;;) {
-                rel = ld_relaxed_u64(&ctl->release);
-                if ((rel >> 43) == want) break;
-                if ((++spins & 15u) == 0) {
-                    if (ld_volatile(&ctl->err) != 0) { ok = 0; break; }
-                    if (globaltimer() > t_end) { set_error(ctl, -5 /*BM_ERR_TIMEOUT*/); ok = 0; break; }
-                }
+        unsigned long long* w = &ctl->arrive[b % 3][0];
+        red_add_release_u64(w, inc);
+        unsigned long long t_end = globaltimer() + (unsigned long long)wait_ns;
+        if (t_end > deadline) t_end = deadline;
+        unsigned spins = 0;
+        unsigned long long v;
+        for (;;) {
+            v = ld_acquire_u64(w);
+            if ((v & 0x7FFull) == (unsigned long long)gridDim.x) break;
+            if ((++spins & 15u) == 0) {
+                if (ld_volatile(&ctl->err) != 0) { ok = 0; break; }
+                if (globaltimer() > t_end) { set_error(ctl, -5 /*BM_ERR_TIMEOUT*/); ok = 0; break; }
             }
-            asm volatile("fence.acq_rel.gpu;" ::: "memory");
         }
-        sm.bc_a = (int)(rel & 0xFFFFFFFFull);
-        sm.bc_b = (int)((rel >> 32) & 0x7FFull);
+        if (blockIdx.x == 0) st_relaxed_u64(&ctl->arrive[(b + 2) % 3][0], 0ull);
+        sm.bc_a = (int)((v >> 22) & 0xFFFFFFFFull);
+        sm.bc_b = (int)((v >> 11) & 0x7FFull);
         if (extra_ptr) sm.bc_c = ld_volatile(extra_ptr);
         if (extra_ptr2) sm.bc_d = ld_volatile(extra_ptr2);
         sm.npush = 0;

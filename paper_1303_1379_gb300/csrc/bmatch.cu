@@ -356,7 +356,8 @@ int32_t configure(bm_ctx* ctx) {
         int cap = 2048 / ctx->block;  // at most 2048 resident threads per SM
         if (ctx->opt.blocks_per_sm > 0 && ctx->opt.blocks_per_sm < cap) cap = ctx->opt.blocks_per_sm;
         if (per_sm > cap) per_sm = cap;
-        if (per_sm < 1) return BM_ERR_UNSUPPORTED;
+        while (per_sm > 1 && per_sm * ctx->num_sms > 2047) --per_sm;  // barrier words count blocks in 11 bits
+        if (per_sm < 1 || per_sm * ctx->num_sms > 2047) return BM_ERR_UNSUPPORTED;
         ctx->coop_grid[wr] = per_sm * ctx->num_sms;
     }
     return BM_OK;
