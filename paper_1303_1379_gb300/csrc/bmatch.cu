@@ -933,6 +933,8 @@ int32_t noalloc_setup(int dev, NoallocDevice* out) {
         }
         if (!coop || per_sm < 1) return BM_ERR_UNSUPPORTED;
         if (per_sm > 2048 / kDefaultBlock) per_sm = 2048 / kDefaultBlock;
+        while (per_sm > 1 && per_sm * sms > 2047) --per_sm;  // barrier words count blocks in 11 bits
+        if (per_sm * sms > 2047) return BM_ERR_UNSUPPORTED;
         d.scratch = (unsigned char*)ptr;
         d.grid = per_sm * sms;
         d.block = kDefaultBlock;
