@@ -16,7 +16,18 @@
 //  * Insertions are claimed with a test-then-CAS on the column's level entry;
 //    the single winner writes pred/root and appends the column.  The paper's
 //    atomic-free writes let several threads insert the same column; a queue
-//    needs exactly one.
+//    needs exactly one.  The persistent kernel of a context claims the
+//    column's matched row instead (below), one dependent load earlier.
+//  * A matched column is reached only through its matched row, so "column c
+//    visited" is "row cmatch[c] claimed".  With a row-indexed stamp array
+//    rvis (stamp = a number unique to the phase, growing across phases and
+//    calls), a level of at most RV_MAX_Q columns claims with
+//    atomicMax(rvis[r], stamp), issued blind together with the rmatch[r]
+//    load: one dependent round trip less than load-rmatch-then-CAS-level on
+//    the deep, narrow, latency-bound levels.  Larger levels, which are
+//    bandwidth-bound, claim on the column's level as before (measured faster
+//    there) and their winners also stamp the row, so both kinds of level see
+//    the same visited set; every winner writes the column's level.
 //  * Free rows are claimed with a CAS -1 -> -2 on rmatch (the paper's plain
 //    store of -2), so every endpoint has exactly one predecessor and is
 //    appended once to an endpoint list; Alternate walks that list instead of
@@ -42,6 +53,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int MAX_BLOCK = 1024;
 constexpr int QBUF = 2048;  // per-block append buffer (entries)
 constexpr int ILP = 4;      // edges per thread in flight
+constexpr int RV_MAX_Q = 32768;  // largest level (columns) that claims through row stamps
 
 // Control block in device memory, cleared before every launch.  Per-step
 // counters rotate over three slots: step s appends to slot s % 3 and clears
@@ -88,6 +100,7 @@ struct Params {
     int2* queue;         // (column, root) of the current phase, level by level
     int2* queue2;        // second queue buffer: roots of the next phase (nullable)
     int32_t* endpoints;  // rows claimed as path ends in the current phase
+    int32_t* rvis;       // per row: stamp of the phase that claimed its column (nullable: level-based claims)
     Ctl* ctl;
     int32_t mode;        // 0 APFB, 1 APsB
     int32_t one_ep;      // GPUBFS-WR: one endpoint per root (-(row) in the root slot)
@@ -98,6 +111,7 @@ struct Params {
     int32_t* profile;    // per phase: levels, endpoints, first and last level with an endpoint (nullable)
     long long wait_ns;   // limit of one barrier wait
     long long total_ns;  // limit of the whole launch
+    int32_t stamp_base;  // rvis stamp of phase k is stamp_base + k (k >= 1); above every stamp in rvis
 };
 
 // Per-block shared state of the steps.
@@ -272,6 +286,17 @@ struct Counters {  // per-thread, flushed once per launch (32 bits: a thread's s
     unsigned cols, edges, fixes, em, alt;
 };
 
+// Adds every thread's v to *dst with one atomic per warp.  Call with the whole
+// warp converged (the grid-wide steps below call it once, at their end), so
+// that the steps run once per phase do not keep counters live across the
+// kernel.
+__device__ __forceinline__ void add_to_counter(long long* dst, unsigned v) {
+    unsigned long long a = v;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) a += __shfl_down_sync(FULL, a, s);
+    if ((threadIdx.x & 31) == 0 && a) atomicAdd((unsigned long long*)dst, a);
+}
+
 // ------------------------------------------------------------------ InitBfsArray
 // Algorithm 1 InitBfsArray (+ GPUBFS-WR root init, Section 3): level L0 for
 // unmatched columns, L0 - 1 for matched ones; root[c] = c for unmatched ones
@@ -284,6 +309,7 @@ template <bool WR>
 __device__ __forceinline__ void step_init(const Params& p, int2* q, int slot, Counters& cnt, Smem& sm) {
     const int nc = p.nc;
     int nfree = 0, niso = 0;
+    unsigned fixes = 0;
     for (int base = blockIdx.x * blockDim.x; base < nc; base += gridDim.x * blockDim.x) {  // block-uniform
         const int c = base + threadIdx.x;
         if (c < nc) {
@@ -291,7 +317,7 @@ __device__ __forceinline__ void step_init(const Params& p, int2* q, int slot, Co
             if (r >= 0 && __ldcg(&p.rmatch[r]) != c) {
                 __stcg(&p.cmatch[c], -1);
                 r = -1;
-                cnt.fixes++;
+                ++fixes;
             }
             const bool is_free = (r < 0);
             __stcg(&p.level[c], is_free ? L0 : L0 - 1);
@@ -311,6 +337,7 @@ __device__ __forceinline__ void step_init(const Params& p, int2* q, int slot, Co
     }
     if ((threadIdx.x & 31) == 0 && nfree) atomicAdd(&p.ctl->ecnt[slot], nfree);
     if ((threadIdx.x & 31) == 0 && niso) atomicAdd(&p.ctl->icnt[slot], niso);
+    add_to_counter(&p.ctl->fix_repairs, fixes);
 }
 
 // Between phases in the one-endpoint GPUBFS-WR mode (where Alternate's walks
@@ -397,11 +424,15 @@ __device__ __forceinline__ void tile_load(const Params& p, const int2* queue, in
 // Visits every edge of the loaded tile (Algorithm 2 / 4 loop body), ILP edges
 // per thread with their loads in flight together.  push_col(cm) appends a
 // column inserted at level lvl + 1, push_end(r) an endpoint row.
-// direct: claim with the CAS alone (small frontiers: saves a dependent load);
-// otherwise test the level first and CAS only unvisited columns.
-template <bool WR, class PushCol, class PushEnd, bool NC = true>
+// direct: claim with the atomic alone (small frontiers: saves a dependent load);
+// otherwise test first and claim only unvisited columns.  RV (row stamps
+// p.rvis available): use_rv claims through the row stamps with `stamp` (see
+// the header comment); otherwise claims go to the column's level entry and,
+// with RV, the winner also stamps the row.
+template <bool WR, class PushCol, class PushEnd, bool NC = true, bool RV = false>
 __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, bool direct, Smem& sm,
-                                           Counters& cnt, PushCol push_col, PushEnd push_end) {
+                                           Counters& cnt, PushCol push_col, PushEnd push_end, int stamp = 0,
+                                           bool use_rv = false) {
     const int T = blockDim.x;
     const int t = threadIdx.x;
     const int total = sm.total;
@@ -424,10 +455,23 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
                 }
             }
         }
+        if (RV && use_rv) {
+            // rmatch[r] and the claim of the row: independent, in flight together
 #pragma unroll
-        for (int u = 0; u < ILP; ++u) cm[u] = (own[u] >= 0) ? __ldcg(&p.rmatch[r[u]]) : -3;
+            for (int u = 0; u < ILP; ++u) {
+                cm[u] = -3;
+                lv[u] = stamp;
+                if (own[u] >= 0) {
+                    cm[u] = __ldcg(&p.rmatch[r[u]]);
+                    lv[u] = atomicMax(&p.rvis[r[u]], stamp);
+                }
+            }
+        } else {
 #pragma unroll
-        for (int u = 0; u < ILP; ++u) lv[u] = (cm[u] >= 0 && !direct) ? __ldcg(&p.level[cm[u]]) : L0 - 1;
+            for (int u = 0; u < ILP; ++u) cm[u] = (own[u] >= 0) ? __ldcg(&p.rmatch[r[u]]) : -3;
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) lv[u] = (cm[u] >= 0 && !direct) ? __ldcg(&p.level[cm[u]]) : L0 - 1;
+        }
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
             if (own[u] < 0) continue;
@@ -437,7 +481,14 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
             if (cm[u] >= 0) {
                 cnt.em++;
                 // matched row: its column joins the next level unless already reached
-                if (lv[u] == L0 - 1 && atomicCAS(&p.level[cm[u]], L0 - 1, lvl + 1) == L0 - 1) {
+                bool won;
+                if (RV && use_rv) won = lv[u] < stamp;
+                else won = lv[u] == L0 - 1 && atomicCAS(&p.level[cm[u]], L0 - 1, lvl + 1) == L0 - 1;
+                if (won) {
+                    if (RV) {
+                        if (use_rv) __stcg(&p.level[cm[u]], lvl + 1);
+                        else __stcg(&p.rvis[r[u]], stamp);
+                    }
                     __stcg(&p.pred[r[u]], col);
                     if (WR) __stcg(&p.root[cm[u]], rt);
                     push_col(make_int2(cm[u], rt));
@@ -471,9 +522,9 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
 // ep_phase (the phase's running count).  Frontiers of at most one tile per
 // block (the deep, narrow levels of long augmenting paths) take their tile
 // from blockIdx.x alone and claim columns by CAS without a test load.
-template <bool WR>
+template <bool WR, bool RV = false>
 __device__ __forceinline__ void step_expand(const Params& p, int2* queue, int qb, int qe, int lvl, int slot,
-                                            Counters& cnt, Smem& sm) {
+                                            Counters& cnt, Smem& sm, int stamp = 0) {
     const int q = qe - qb;
     // tile width: spread small frontiers over many blocks, never above blockDim
     int tw = (q + gridDim.x - 1) / gridDim.x;
@@ -487,7 +538,8 @@ __device__ __forceinline__ void step_expand(const Params& p, int2* queue, int qb
     for (int tile = blockIdx.x; tile < ntiles;) {  // block-uniform
         tile_load<WR>(p, queue, qb, q, tile * tw, tw, sm, cnt, narrow ? nullptr : &p.ctl->tcnt[slot]);
         const int next_tile = narrow ? ntiles : sm.tile;
-        tile_edges<WR>(p, tw, lvl, narrow, sm, cnt, push_col, push_end);
+        tile_edges<WR, decltype(push_col), decltype(push_end), true, RV>(p, tw, lvl, narrow, sm, cnt, push_col,
+                                                                          push_end, stamp, q <= RV_MAX_Q);
         flush_block(p, queue, sm, qe, slot);
         tile = next_tile;
     }
@@ -502,6 +554,7 @@ __device__ __forceinline__ void step_expand(const Params& p, int2* queue, int qb
 __device__ __forceinline__ void step_alternate(const Params& p, int n_ep, int cap, Counters& cnt) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthr = gridDim.x * blockDim.x;
+    unsigned steps_done = 0;
     for (int i = tid; i < n_ep; i += nthr) {
         int r = __ldcg(&p.endpoints[i]);
         int steps = 0;
@@ -513,10 +566,11 @@ __device__ __forceinline__ void step_alternate(const Params& p, int n_ep, int ca
             if (r2 >= 0 && __ldcg(&p.pred[r2]) == c) break;
             st_volatile(&p.cmatch[c], r);
             __stcg(&p.rmatch[r], c);
-            cnt.alt++;
+            ++steps_done;
             r = r2;
         }
     }
+    add_to_counter(&p.ctl->alt_steps, steps_done);
 }
 
 // ------------------------------------------------------------------ FixMatching
@@ -526,14 +580,16 @@ __device__ __forceinline__ void step_alternate(const Params& p, int n_ep, int ca
 __device__ __forceinline__ void step_fix_rows(const Params& p, Counters& cnt) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthr = gridDim.x * blockDim.x;
+    unsigned fixes = 0;
     for (int r = tid; r < p.nr; r += nthr) {
         const int m = __ldcg(&p.rmatch[r]);
         if (m == -1) continue;
         if (m < 0 || __ldcg(&p.cmatch[m]) != r) {
             __stcg(&p.rmatch[r], -1);
-            cnt.fixes++;
+            ++fixes;
         }
     }
+    add_to_counter(&p.ctl->fix_repairs, fixes);
 }
 
 // Gives back the rows a BFS-only pass claimed (inspection entry point).

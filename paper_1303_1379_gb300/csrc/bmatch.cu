@@ -33,17 +33,30 @@ constexpr int kProfileCap = 4096;
 
 // ------------------------------------------------------------------ kernels
 
-// One launch per match: Algorithm 1 with both loops on the device.
-template <bool WR>
+// Statistics of a persistent launch, kept by its leader thread in shared
+// memory (not in every thread's registers: the BFS loop needs them for
+// nothing else).
+struct LeaderStats {
+    unsigned long long t_start;
+    long long levels_total, levels_max, eps_total, ins_total;
+    int levels, first_ep, last_ep;
+};
+
+// One launch per match: Algorithm 1 with both loops on the device.  RV: small
+// BFS levels claim columns through the row stamps p.rvis (a context's
+// launches); without it every level claims through the column levels (the
+// allocation-free entry point).
+template <bool WR, bool RV>
 __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
     using namespace bmd;
     Ctl* ctl = p.ctl;
     __shared__ Smem sm;
+    __shared__ LeaderStats ls;  // written by the leader thread only
     if (threadIdx.x == 0) { sm.qn = 0; sm.npush = 0; sm.has_ep = 0; }
     int bid = 0;  // grid barriers passed
-    const unsigned long long t_start = globaltimer();
-    const unsigned long long deadline = t_start + (unsigned long long)p.total_ns;
+    const unsigned long long deadline = globaltimer() + (unsigned long long)p.total_ns;
     const bool leader = (blockIdx.x == 0 && threadIdx.x == 0);
+    if (leader) ls = LeaderStats{globaltimer(), 0, 0, 0, 0, 0, 0, 0};
     // one-endpoint GPUBFS-WR: no FixMatching passes, roots carried to the next phase
     const bool incr = WR && p.one_ep && p.queue2 != nullptr && !p.bfs_only;
     int2* qcur = p.queue;
@@ -55,7 +68,6 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
     int status = 0;
     int n_roots = 0;
     int iso_free = 0;
-    long long levels_total = 0, levels_max = 0, eps_total = 0, ins_total = 0;
     if (ld_volatile(&ctl->err) != 0) goto out;  // input validation failed before launch
     {
         // ---- InitBfsArray (+ column half of FixMatching)
@@ -83,20 +95,23 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
         ++phases;
 
         // ---- BFS, level by level (Algorithm 1 inner loop)
-        int qb = 0, qe = n_roots, lvl = L0, levels = 0, first_ep = 0, last_ep = 0, tail = n_roots;
+        int qb = 0, qe = n_roots, lvl = L0, tail = n_roots;
+        if (leader) { ls.levels = 0; ls.first_ep = 0; ls.last_ep = 0; }
         for (;;) {
             const int s2 = step++;
             if (leader) { ctl->qcnt[(s2 + 1) % 3] = 0; ctl->ecnt[(s2 + 1) % 3] = 0; ctl->icnt[(s2 + 1) % 3] = 0; ctl->tcnt[(s2 + 1) % 3] = 0; }
-            step_expand<WR>(p, qcur, qb, qe, lvl, s2 % 3, cnt, sm);
+            step_expand<WR, RV>(p, qcur, qb, qe, lvl, s2 % 3, cnt, sm, p.stamp_base + phases);
             if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
             const int nq = sm.bc_a;           // columns inserted at this level
             const bool found = sm.bc_b > 0;   // some block claimed an endpoint
-            ++levels;
-            if (found) {
-                if (first_ep == 0) first_ep = levels;
-                last_ep = levels;
+            if (leader) {
+                const int lv_now = ++ls.levels;
+                if (found) {
+                    if (ls.first_ep == 0) ls.first_ep = lv_now;
+                    ls.last_ep = lv_now;
+                }
+                ls.ins_total += nq;
             }
-            ins_total += nq;
             tail = qe + nq;
             if (nq == 0) break;              // no vertex inserted
             if (p.mode == 1 && found) break;  // APsB: stop at the first level with a path
@@ -107,17 +122,17 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
         if (threadIdx.x == 0) sm.bc_c = ld_volatile(&ctl->ep_phase);  // all appends precede the barrier
         __syncthreads();
         const int n_ep = sm.bc_c;
-        levels_total += levels;
-        if (levels > levels_max) levels_max = levels;
-        eps_total += n_ep;
         if (leader) {
+            ls.levels_total += ls.levels;
+            if (ls.levels > ls.levels_max) ls.levels_max = ls.levels;
+            ls.eps_total += n_ep;
             ctl->n_endpoints_last = n_ep;
             if (p.profile && phases <= p.profile_cap) {
                 int32_t* pr = p.profile + 4 * (phases - 1);
-                pr[0] = levels;
+                pr[0] = ls.levels;
                 pr[1] = n_ep;
-                pr[2] = first_ep;
-                pr[3] = last_ep;
+                pr[2] = ls.first_ep;
+                pr[3] = ls.last_ep;
             }
         }
 
@@ -167,11 +182,11 @@ out:
         ctl->status = err != 0 ? err : status;
         ctl->card = card;
         ctl->phases = phases + 1;  // counting the final search that found nothing
-        ctl->levels = levels_total;
-        ctl->max_levels = levels_max;
-        ctl->endpoints = eps_total;
-        ctl->inserted = ins_total;
-        ctl->kernel_ns = (long long)(globaltimer() - t_start);
+        ctl->levels = ls.levels_total;
+        ctl->max_levels = ls.levels_max;
+        ctl->endpoints = ls.eps_total;
+        ctl->inserted = ls.ins_total;
+        ctl->kernel_ns = (long long)(globaltimer() - ls.t_start);
     }
 }
 
@@ -303,13 +318,15 @@ struct bm_ctx {
     int2* queue = nullptr;
     int2* queue2 = nullptr;  // roots of the next phase (one-endpoint GPUBFS-WR)
     int32_t* endpoints = nullptr;
+    int32_t* rvis = nullptr;     // per-row claim stamps of the persistent kernel
+    long long stamp_next = 0;    // every stamp in rvis is below stamp_next + 1
     int32_t* profile = nullptr;  // kProfileCap phases x 4
     Ctl* ctl = nullptr;
     Ctl* h_ctl = nullptr;  // pinned mirror
     int32_t sticky = 0;
     int device = 0;
     int num_sms = 0;
-    int coop_grid[2] = {0, 0};  // blocks of k_match<false>, k_match<true>
+    int coop_grid[2] = {0, 0};  // blocks of k_match<false, true>, k_match<true, true>
     int block = kDefaultBlock;
 };
 
@@ -350,8 +367,8 @@ int32_t configure(bm_ctx* ctx) {
     ctx->block = ctx->opt.block_size ? ctx->opt.block_size : kDefaultBlock;
     for (int wr = 0; wr < 2; ++wr) {
         int per_sm = 0;
-        cudaError_t e = wr ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true>, ctx->block, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<false>, ctx->block, 0);
+        cudaError_t e = wr ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true, true>, ctx->block, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<false, true>, ctx->block, 0);
         if (e != cudaSuccess) return cuda_fail(ctx, e);
         int cap = 2048 / ctx->block;  // at most 2048 resident threads per SM
         if (ctx->opt.blocks_per_sm > 0 && ctx->opt.blocks_per_sm < cap) cap = ctx->opt.blocks_per_sm;
@@ -377,6 +394,7 @@ Params make_params(bm_ctx* ctx, bool bfs_only) {
     p.queue = ctx->queue;
     p.queue2 = ctx->queue2;
     p.endpoints = ctx->endpoints;
+    p.rvis = ctx->rvis;
     p.ctl = ctx->ctl;
     p.mode = ctx->opt.mode;
     p.one_ep = ctx->opt.wr_one_endpoint;
@@ -520,9 +538,18 @@ int32_t run(bm_ctx* ctx, bool bfs_only) {
         if (rc < 0 && ctx->sticky == 0) ctx->sticky = rc;
         return rc < 0 ? rc : ctx->h_ctl->status;
     }
+    // row stamps of this launch: stamp_next + 1 ... stamp_next + max_phases; the
+    // array is cleared when they would pass INT32_MAX
+    const long long span = (long long)p.max_phases + 1;
+    if (ctx->stamp_next + span >= 0x7fffffffLL) {
+        BM_CUDA(ctx, cudaMemsetAsync(ctx->rvis, 0, 4 * (size_t)(ctx->nr ? ctx->nr : 1), ctx->stream));
+        ctx->stamp_next = 0;
+    }
+    p.stamp_base = (int32_t)ctx->stamp_next;
+    ctx->stamp_next += span;
     void* args[] = {&p};
-    cudaError_t e = wr ? cudaLaunchCooperativeKernel((const void*)k_match<true>, ctx->coop_grid[1], ctx->block, args, 0, ctx->stream)
-                       : cudaLaunchCooperativeKernel((const void*)k_match<false>, ctx->coop_grid[0], ctx->block, args, 0, ctx->stream);
+    cudaError_t e = wr ? cudaLaunchCooperativeKernel((const void*)k_match<true, true>, ctx->coop_grid[1], ctx->block, args, 0, ctx->stream)
+                       : cudaLaunchCooperativeKernel((const void*)k_match<false, true>, ctx->coop_grid[0], ctx->block, args, 0, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     return BM_OK;
 }
@@ -617,7 +644,8 @@ int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* co
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
     if (!coop) { delete ctx; return BM_ERR_UNSUPPORTED; }
 
-    // arena: [ctl][rmatch nr][cmatch nc][level nc][root nc][pred nr][queue nc][endpoints nr][csr?]
+    // arena: [ctl][rmatch nr][cmatch nc][level nc][root nc][pred nr][queue nc][queue2 nc][endpoints nr]
+    //        [rvis nr][profile][csr?]
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t nr1 = (size_t)(n_rows ? n_rows : 1), nc1 = (size_t)(n_cols ? n_cols : 1);
     size_t off_ctl = 0;
@@ -629,7 +657,8 @@ int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* co
     size_t off_q = off_pd + al(4 * nr1);
     size_t off_q2 = off_q + al(8 * nc1);
     size_t off_ep = off_q2 + al(8 * nc1);
-    size_t off_pf = off_ep + al(4 * nr1);
+    size_t off_rv = off_ep + al(4 * nr1);
+    size_t off_pf = off_rv + al(4 * nr1);
     size_t off_cp = off_pf + al(4 * 4 * (size_t)kProfileCap);
     size_t total = off_cp;
     const bool own = (col_ptr == nullptr);
@@ -659,6 +688,7 @@ int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* co
     ctx->queue = (int2*)(a + off_q);
     ctx->queue2 = (int2*)(a + off_q2);
     ctx->endpoints = (int32_t*)(a + off_ep);
+    ctx->rvis = (int32_t*)(a + off_rv);
     ctx->profile = (int32_t*)(a + off_pf);
     if (own) {
         ctx->owns_csr = true;
@@ -674,7 +704,8 @@ int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* co
     if (cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), st) != cudaSuccess ||
         cudaMemsetAsync(ctx->rmatch, 0xff, 4 * nr1, st) != cudaSuccess ||
         cudaMemsetAsync(ctx->cmatch, 0xff, 4 * nc1, st) != cudaSuccess ||
-        cudaMemsetAsync(ctx->pred, 0xff, 4 * nr1, st) != cudaSuccess) {
+        cudaMemsetAsync(ctx->pred, 0xff, 4 * nr1, st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->rvis, 0, 4 * nr1, st) != cudaSuccess) {
         cuda_fail(ctx, cudaGetLastError());
         bm_destroy(ctx);
         return BM_ERR_CUDA;
@@ -906,7 +937,7 @@ constexpr int kMaxDevices = 64;
 struct NoallocDevice {
     bool ready;
     unsigned char* scratch;  // device address of g_noalloc_scratch on this device
-    int grid;                // cooperative grid of k_match<true>
+    int grid;                // cooperative grid of k_match<true, false>
     int block;
     int sms;
 };
@@ -927,7 +958,7 @@ int32_t noalloc_setup(int dev, NoallocDevice* out) {
         int sms = 0, coop = 0, per_sm = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true>, kDefaultBlock, 0) != cudaSuccess) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true, false>, kDefaultBlock, 0) != cudaSuccess) {
             (void)cudaGetLastError();
             return BM_ERR_CUDA;
         }
@@ -1010,7 +1041,7 @@ extern "C" int32_t bm_match_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
     k_check_matching<<<g2, d.block, 0, st>>>(n_rows, n_cols, rmatch, cmatch, ctl);
     if (cudaGetLastError() != cudaSuccess) return BM_ERR_CUDA;
     void* args[] = {&p};
-    if (cudaLaunchCooperativeKernel((const void*)k_match<true>, d.grid, d.block, args, 0, st) != cudaSuccess) {
+    if (cudaLaunchCooperativeKernel((const void*)k_match<true, false>, d.grid, d.block, args, 0, st) != cudaSuccess) {
         (void)cudaGetLastError();
         return BM_ERR_CUDA;
     }
