@@ -101,6 +101,7 @@ struct Params {
     int2* queue2;        // second queue buffer: roots of the next phase (nullable)
     int32_t* endpoints;  // rows claimed as path ends in the current phase
     int32_t* rvis;       // per row: stamp of the phase that claimed its column (nullable: level-based claims)
+    int2* crec;          // per column inserted this phase: (parent column, matched row); roots (-1, -1) (nullable)
     Ctl* ctl;
     int32_t mode;        // 0 APFB, 1 APsB
     int32_t one_ep;      // GPUBFS-WR: one endpoint per root (-(row) in the root slot)
@@ -323,6 +324,7 @@ __device__ __forceinline__ void step_init(const Params& p, int2* q, int slot, Co
             __stcg(&p.level[c], is_free ? L0 : L0 - 1);
             if (WR) __stcg(&p.root[c], is_free ? c : -1);
             if (is_free) {
+                if (p.crec) __stcg(&p.crec[c], make_int2(-1, -1));
                 ++nfree;
                 if (__ldg(&p.col_ptr[c + 1]) > __ldg(&p.col_ptr[c])) push_block(p, q, sm, 0, slot, make_int2(c, c));
                 else ++niso;
@@ -491,6 +493,7 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
                     }
                     __stcg(&p.pred[r[u]], col);
                     if (WR) __stcg(&p.root[cm[u]], rt);
+                    if (RV) __stcg(&p.crec[cm[u]], make_int2(col, r[u]));
                     push_col(make_int2(cm[u], rt));
                 }
             } else if (cm[u] == -1) {
@@ -568,6 +571,35 @@ __device__ __forceinline__ void step_alternate(const Params& p, int n_ep, int ca
             __stcg(&p.rmatch[r], c);
             ++steps_done;
             r = r2;
+        }
+    }
+    add_to_counter(&p.ctl->alt_steps, steps_done);
+}
+
+// Alternate for disjoint search trees (one endpoint per root, Section 3's
+// refinement): the walks cannot meet, so a walk needs no meeting check and
+// follows the per-column records written by the BFS, one 8-byte load per
+// step: column c on the path has (parent column, its old matched row); c is
+// rematched to the row below it, and the walk continues from the old row's
+// parent.  The root's record is (-1, -1).
+__device__ __forceinline__ void step_alternate_disjoint(const Params& p, int n_ep, int cap) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthr = gridDim.x * blockDim.x;
+    unsigned steps_done = 0;
+    for (int i = tid; i < n_ep; i += nthr) {
+        int r = __ldcg(&p.endpoints[i]);
+        int c = __ldcg(&p.pred[r]);
+        int steps = 0;
+        for (;;) {
+            if (++steps > cap) { set_error(p.ctl, -4 /*BM_ERR_ITER_LIMIT*/); break; }
+            if ((unsigned)c >= (unsigned)p.nc) { set_error(p.ctl, -7 /*BM_ERR_STATE*/); break; }
+            const int2 rec = __ldcg(&p.crec[c]);
+            __stcg(&p.cmatch[c], r);
+            __stcg(&p.rmatch[r], c);
+            ++steps_done;
+            if (rec.y < 0) break;  // c was the root
+            r = rec.y;
+            c = rec.x;
         }
     }
     add_to_counter(&p.ctl->alt_steps, steps_done);

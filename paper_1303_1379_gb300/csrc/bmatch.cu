@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
         if (n_ep == 0) break;  // no augmenting path: the matching is maximum (Berge)
 
         // ---- Alternate (Algorithm 3); the walk is at most as long as the forest
-        step_alternate(p, n_ep, tail + 2, cnt);
+        if (RV && incr) step_alternate_disjoint(p, n_ep, tail + 2);
+        else step_alternate(p, n_ep, tail + 2, cnt);
         if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
         if (incr) {
             // ---- next phase's roots: the unmatched ones among this phase's roots
@@ -319,6 +320,7 @@ struct bm_ctx {
     int2* queue2 = nullptr;  // roots of the next phase (one-endpoint GPUBFS-WR)
     int32_t* endpoints = nullptr;
     int32_t* rvis = nullptr;     // per-row claim stamps of the persistent kernel
+    int2* crec = nullptr;        // per-column (parent column, matched row) of the last search
     long long stamp_next = 0;    // every stamp in rvis is below stamp_next + 1
     int32_t* profile = nullptr;  // kProfileCap phases x 4
     Ctl* ctl = nullptr;
@@ -395,6 +397,7 @@ Params make_params(bm_ctx* ctx, bool bfs_only) {
     p.queue2 = ctx->queue2;
     p.endpoints = ctx->endpoints;
     p.rvis = ctx->rvis;
+    p.crec = ctx->crec;
     p.ctl = ctx->ctl;
     p.mode = ctx->opt.mode;
     p.one_ep = ctx->opt.wr_one_endpoint;
@@ -645,7 +648,7 @@ int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* co
     if (!coop) { delete ctx; return BM_ERR_UNSUPPORTED; }
 
     // arena: [ctl][rmatch nr][cmatch nc][level nc][root nc][pred nr][queue nc][queue2 nc][endpoints nr]
-    //        [rvis nr][profile][csr?]
+    //        [rvis nr][crec nc][profile][csr?]
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t nr1 = (size_t)(n_rows ? n_rows : 1), nc1 = (size_t)(n_cols ? n_cols : 1);
     size_t off_ctl = 0;
@@ -658,7 +661,8 @@ int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* co
     size_t off_q2 = off_q + al(8 * nc1);
     size_t off_ep = off_q2 + al(8 * nc1);
     size_t off_rv = off_ep + al(4 * nr1);
-    size_t off_pf = off_rv + al(4 * nr1);
+    size_t off_cr = off_rv + al(4 * nr1);
+    size_t off_pf = off_cr + al(8 * nc1);
     size_t off_cp = off_pf + al(4 * 4 * (size_t)kProfileCap);
     size_t total = off_cp;
     const bool own = (col_ptr == nullptr);
@@ -689,6 +693,7 @@ int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* co
     ctx->queue2 = (int2*)(a + off_q2);
     ctx->endpoints = (int32_t*)(a + off_ep);
     ctx->rvis = (int32_t*)(a + off_rv);
+    ctx->crec = (int2*)(a + off_cr);
     ctx->profile = (int32_t*)(a + off_pf);
     if (own) {
         ctx->owns_csr = true;
