@@ -100,3 +100,18 @@ def test_batch_rejects_invalid_graph():
     with pytest.raises(bmatch.BMError) as e:
         bmatch.Batch(b.n_rows, b.n_cols, b.row_off, b.col_off, b.edge_off, b.col_ptr, bad)
     assert e.value.status == bmatch.BM_ERR_INVALID_CSR
+
+
+@pytest.mark.slow
+def test_batch_full_size_4096_graphs():
+    """The batched workload at full size, in the launch geometry the benchmark's
+    autotuner settles on (512 threads, 2 blocks per SM) with the cheap matching
+    inside the launch.  The workload is 4,096 graphs, 226 M edges, rows
+    log-uniform in [100, 50,000], seed 3.  Every graph's |M| equals
+    Hopcroft-Karp's, and every graph's slice of the batch matching is valid and
+    carries a Koenig certificate."""
+    b = synth.batch_graphs(4096, seed=3)
+    _, _, want = oracle.hk_batch(b, greedy_first=True)
+    rm, cm, card, st = run_batch(b, greedy=True, block_size=512, blocks_per_sm=2)
+    assert np.array_equal(card, want)
+    check_all(b, rm, cm, card, want)

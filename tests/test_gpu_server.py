@@ -33,6 +33,50 @@ def mixed_requests(n, seed):
     return out
 
 
+def serving_requests(n, seed=4):
+    """Request graphs of the served workload: rows log-uniform in [1,000,
+    1,000,000], columns = rows x U[0.8, 1.25], mean degree U[3, 16], uniform
+    and R-MAT alternating, seeded per request (the benchmark's recipe)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nr = int(np.exp(rng.uniform(np.log(1e3), np.log(1e6))))
+        nc = max(1, int(round(nr * rng.uniform(0.8, 1.25))))
+        mu = rng.uniform(3, 16)
+        if i % 2 == 0:
+            g = synth.uniform_graph(nr, nc, max(1, int(round(2 * mu - 1))), seed=seed * 100000 + i)
+        else:
+            n_ = max(nr, nc)
+            g = synth.rmat_graph(int(np.ceil(np.log2(n_))), int(n_ * mu), seed=seed * 100000 + i, n=n_)
+        out.append(g)
+    return out
+
+
+@pytest.mark.slow
+def test_served_full_size_requests():
+    """Requests of the served workload at full size (up to a million rows
+    and 16 M edges each), three copies of each of 16 graphs submitted at once,
+    so that copies run concurrently with one another and with the other
+    graphs.  Every result equals Hopcroft-Karp's |M|, and every matching is
+    valid and carries a Koenig certificate."""
+    reqs = serving_requests(16)
+    want = [oracle.hopcroft_karp(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)[2] for g in reqs]
+    with bmatch.Server(keep_results=1, pool_bytes=8 << 30) as srv:
+        ids = [(k, srv.submit(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)) for _ in range(3)
+               for k, g in enumerate(reqs)]
+        for k, rid in ids:
+            g = reqs[k]
+            info = srv.wait(rid, timeout_s=120)
+            assert info["state"] == bmatch.BM_REQ_DONE and info["status"] == 0
+            assert info["card"] == want[k], (k, info["card"], want[k])
+            rm = np.empty(g.n_rows, np.int32)
+            cm = np.empty(g.n_cols, np.int32)
+            srv.fetch(rid, rm, cm)
+            assert_maximum(g, rm, cm, info["card"], want[k])
+            srv.release(rid)
+        assert srv.stats()["pool_used"] == 0
+
+
 def test_results_same_alone_and_in_the_mix():
     reqs = mixed_requests(40, seed=4)
     want = [oracle.hopcroft_karp(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)[2] for g in reqs]
