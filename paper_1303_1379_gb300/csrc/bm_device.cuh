@@ -423,6 +423,46 @@ __device__ __forceinline__ void tile_load(const Params& p, const int2* queue, in
     __syncthreads();
 }
 
+// tile_load for tiles of 2 x blockDim entries (two per thread; 2 x blockDim
+// <= MAX_BLOCK): the one-block-per-graph routine, where a level's tiles run
+// one after another in one block, gets twice the columns (and their loads)
+// in flight per tile.  Ends with __syncthreads.
+template <bool WR, bool NC = true>
+__device__ __forceinline__ void tile_load2(const Params& p, const int2* queue, int qb, int q, int first, Smem& sm,
+                                           Counters& cnt) {
+    const int t = threadIdx.x;
+    int c[2], beg[2], deg[2], rt[2], rl[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int i = first + 2 * t + u;
+        c[u] = -1; beg[u] = 0; deg[u] = 0; rt[u] = -1; rl[u] = L0;
+        if (i < q) {
+            const int2 ent = __ldcg(&queue[qb + i]);
+            c[u] = ent.x;
+            rt[u] = ent.y;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        if (c[u] >= 0) {
+            beg[u] = ld_csr<NC>(&p.col_ptr[c[u]]);
+            deg[u] = ld_csr<NC>(&p.col_ptr[c[u] + 1]) - beg[u];
+            if (WR) rl[u] = __ldcg(&p.level[rt[u]]);
+        }
+    }
+    const int off = block_exclusive_scan(deg[0] + deg[1], sm);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        if (WR && rl[u] < L0 - 1) c[u] = -1;  // Algorithm 4: root already served
+        if (c[u] >= 0) cnt.cols++;
+        sm.off[2 * t + u] = off + (u ? deg[0] : 0);
+        sm.beg[2 * t + u] = beg[u];
+        sm.col[2 * t + u] = c[u];
+        sm.root[2 * t + u] = rt[u];
+    }
+    __syncthreads();
+}
+
 // Visits every edge of the loaded tile (Algorithm 2 / 4 loop body), ILP edges
 // per thread with their loads in flight together.  push_col(cm) appends a
 // column inserted at level lvl + 1, push_end(r) an endpoint row.
@@ -760,9 +800,12 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
         auto push_end = [&](int v) { p.endpoints[atomicAdd(&sm.qbase, 1)] = v; };
         for (;;) {
             const int q = qe - qb;
-            for (int first = 0; first < q; first += T) {
-                tile_load<WR, NC>(p, p.queue, qb, q, first, T, sm, cnt, nullptr);
-                tile_edges<WR, decltype(push_col), decltype(push_end), NC>(p, T, lvl, q <= T, sm, cnt,
+            const bool wide = q > T && 2 * T <= MAX_BLOCK;  // two queue entries per thread
+            const int tw = wide ? 2 * T : T;
+            for (int first = 0; first < q; first += tw) {
+                if (wide) tile_load2<WR, NC>(p, p.queue, qb, q, first, sm, cnt);
+                else tile_load<WR, NC>(p, p.queue, qb, q, first, T, sm, cnt, nullptr);
+                tile_edges<WR, decltype(push_col), decltype(push_end), NC>(p, tw, lvl, q <= T, sm, cnt,
                                                                            push_col, push_end);
                 __syncthreads();  // sm.off/beg/col/root are reused by the next tile
             }

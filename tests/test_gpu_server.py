@@ -64,16 +64,20 @@ def test_served_full_size_requests():
     with bmatch.Server(keep_results=1, pool_bytes=8 << 30) as srv:
         ids = [(k, srv.submit(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)) for _ in range(3)
                for k, g in enumerate(reqs)]
-        for k, rid in ids:
+        bad = []
+        for j, (k, rid) in enumerate(ids):
             g = reqs[k]
             info = srv.wait(rid, timeout_s=120)
-            assert info["state"] == bmatch.BM_REQ_DONE and info["status"] == 0
-            assert info["card"] == want[k], (k, info["card"], want[k])
-            rm = np.empty(g.n_rows, np.int32)
-            cm = np.empty(g.n_cols, np.int32)
-            srv.fetch(rid, rm, cm)
-            assert_maximum(g, rm, cm, info["card"], want[k])
+            if info["state"] != bmatch.BM_REQ_DONE or info["status"] != 0 or info["card"] != want[k]:
+                bad.append((j, k, g.n_rows, g.nnz, info["state"], info["status"], info["card"], want[k]))
+            else:
+                rm = np.empty(g.n_rows, np.int32)
+                cm = np.empty(g.n_cols, np.int32)
+                srv.fetch(rid, rm, cm)
+                assert_maximum(g, rm, cm, info["card"], want[k])
             srv.release(rid)
+        # (submission, graph, rows, edges, state, status, |M|, expected) of every request that failed
+        assert not bad, bad
         assert srv.stats()["pool_used"] == 0
 
 
