@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-distinct", type=int, default=48)
+    ap.add_argument("--serve-exclusive-min-edges", type=int, default=None,
+                    help="requests with at least this many edges run alone on the whole GPU "
+                         "(0 = never; default: the library's)")
     ap.add_argument("--variant-table", action="store_true",
                     help="print the variant matrix (Table 1 / Fig. 2 quantities) instead")
     ap.add_argument("--table-workloads", default="rmat21,rmat21-rcp,stencil2000,stencil2000-rcp")
@@ -405,7 +408,8 @@ def bench_serving(args, torch, bmatch):
              torch.from_numpy(g.row_idx).pin_memory(), g.nnz) for g in graphs]
     N = args.serve_requests
     mean_edges = float(np.mean([h[4] for h in host]))
-    srv = bmatch.Server(pool_bytes=32 << 30)
+    sopts = {} if args.serve_exclusive_min_edges is None else {"exclusive_min_edges": args.serve_exclusive_min_edges}
+    srv = bmatch.Server(pool_bytes=32 << 30, **sopts)
 
     def run(rate):
         """rate None: all N submitted at once (closed loop saturation)."""
@@ -442,6 +446,7 @@ def bench_serving(args, torch, bmatch):
         if c2 != cards:
             raise SystemExit("served results differ between runs")
     st = srv.stats()
+    srv_opts_threshold = srv.options.exclusive_min_edges
     srv.close()
     distinct = {}
     for i, c in enumerate(cards[:len(host)]):
@@ -449,6 +454,7 @@ def bench_serving(args, torch, bmatch):
     return {"workload": SERVE_WORKLOAD, "distinct_request_graphs": len(host),
             "requests_per_run": N, "mean_edges_per_request": mean_edges, "generate_s": round(t_gen, 1),
             "lambda_max_rps": lam, "runs": runs, "worker_grid": st["grid"], "worker_block": st["block"],
+            "exclusive_min_edges": int(srv_opts_threshold), "requests_run_alone": int(st["exclusive_runs"]),
             "note": "request graphs recycled from the distinct set (host generation of every request "
                     "would dominate the run); each request is uploaded, matched and released on its own"}, \
         graphs, distinct

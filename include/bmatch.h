@@ -322,7 +322,11 @@ typedef struct bm_server_options {
     int64_t idle_timeout_ns; /* workers leave when no block has been busy this long (default 50 ms) */
     int32_t poll_interval_us;/* scheduler sleep when idle (default 5)                             */
     int32_t reserved0;
-    int64_t reserved[4];
+    int64_t exclusive_min_edges; /* requests with at least this many edges run alone on the whole
+                                    GPU (the single-graph persistent kernel, after the workers
+                                    leave; consecutive ones back to back) instead of on one
+                                    worker block; 0 = never (default 262,144)                 */
+    int64_t reserved[3];
 } bm_server_options;
 
 /* Request states reported by bm_server_poll / bm_server_wait. */
@@ -344,7 +348,8 @@ typedef struct bm_request_info {
 typedef struct bm_server_stats {
     int64_t pending, inflight, completed, rejected, worker_launches, pool_bytes, pool_used;
     int32_t grid, block;
-    int64_t reserved[2];
+    int64_t exclusive_runs;  /* requests that ran alone on the whole GPU */
+    int64_t reserved[1];
 } bm_server_stats;
 
 typedef struct bm_server bm_server;

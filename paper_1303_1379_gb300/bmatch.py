@@ -38,7 +38,8 @@ class bm_server_options(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("bfs", ctypes.c_int32), ("keep_results", ctypes.c_int32),
                 ("idle_timeout_ns", ctypes.c_int64), ("poll_interval_us", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("reserved", ctypes.c_int64 * 4)]
+                ("reserved0", ctypes.c_int32), ("exclusive_min_edges", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 3)]
 
 
 class bm_request_info(ctypes.Structure):
@@ -52,7 +53,7 @@ class bm_server_stats(ctypes.Structure):
                 ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
                 ("worker_launches", ctypes.c_int64), ("pool_bytes", ctypes.c_int64),
                 ("pool_used", ctypes.c_int64), ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("reserved", ctypes.c_int64 * 2)]
+                ("exclusive_runs", ctypes.c_int64), ("reserved", ctypes.c_int64 * 1)]
 
 
 BM_REQ_PENDING, BM_REQ_UPLOADING, BM_REQ_RUNNING, BM_REQ_DONE, BM_REQ_CANCELLED = range(5)

@@ -12,6 +12,13 @@
 // picked up by whichever block frees first: their work overlaps on the GPU.
 // Workers leave after an idle period (every wait is bounded) and the
 // scheduler relaunches them when work is published.
+// A request with at least exclusive_min_edges edges would hold one block for
+// tens of milliseconds; it runs alone on the whole GPU instead: the workers
+// are told to leave (they finish the requests they hold), and the checks,
+// the cheap matching and one launch of the single-graph persistent kernel
+// are queued behind them on the same stream.  Consecutive large requests run
+// back to back behind one departure; the next request for the workers waits
+// until they are done (arrival order).
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -27,6 +34,7 @@
 #include <vector>
 
 #include "bm_device.cuh"
+#include "bm_internal.h"
 #include "bmatch.h"
 
 using bmd::Counters;
@@ -255,8 +263,13 @@ struct Request {
 
 size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Device bytes of one request: CSR, matching, workspace.
-size_t request_bytes(int32_t nr, int32_t nc, long long nnz, size_t* offs) {
+constexpr int kOffs = 13;      // arrays of a request's pool region
+constexpr int kExclSlots = 64;  // whole-GPU runs queued at once
+
+// A request's region: its CSR, matching and the workspace of the worker
+// routine (offsets 0-8); requests with at least exclusive_min_edges edges also
+// get the rest of a whole-GPU launch's workspace (9-12).
+size_t request_bytes(int32_t nr, int32_t nc, long long nnz, bool exclusive, size_t* offs) {
     const size_t NR = (size_t)(nr ? nr : 1), NC = (size_t)(nc ? nc : 1);
     size_t o = 0;
     offs[0] = o; o += round256(4 * ((size_t)nc + 1));       // col_ptr
@@ -268,6 +281,13 @@ size_t request_bytes(int32_t nr, int32_t nc, long long nnz, size_t* offs) {
     offs[6] = o; o += round256(8 * NC);                       // queue
     offs[7] = o; o += round256(4 * NR);                       // pred
     offs[8] = o; o += round256(4 * NR);                       // endpoints
+    offs[9] = offs[10] = offs[11] = offs[12] = o;
+    if (exclusive) {
+        offs[9] = o; o += round256(8 * NC);                   // queue2
+        offs[10] = o; o += round256(4 * NR);                  // claim stamps
+        offs[11] = o; o += round256(8 * NC);                  // Alternate records
+        offs[12] = o; o += round256(sizeof(bmd::Ctl));        // control block
+    }
     return o;
 }
 
@@ -298,6 +318,14 @@ struct bm_server {
     std::deque<long long> uploading;
     std::unordered_map<long long, Request> reqs;
     std::vector<long long> ring_owner;  // request id per ring slot, -1 if free
+    // requests running alone on the whole GPU, in launch order: (request id, slot of
+    // excl_ev / h_excl_ctl).  Consecutive ones run back to back behind one departure
+    // of the workers.
+    std::deque<std::pair<long long, int>> excl_runs;
+    std::vector<int> excl_free;            // free slots
+    cudaEvent_t excl_ev[kExclSlots] = {};  // recorded after a launch and the copy of its control block
+    bmd::Ctl* h_excl_ctl = nullptr;        // pinned copies of the control blocks [kExclSlots]
+    long long exclusive_runs = 0;
     long long next_id = 1;
     long long next_ticket = 0;
     int inflight = 0;  // uploading + running
@@ -330,6 +358,49 @@ void launch_workers(bm_server* s) {
     s->launches++;
 }
 
+// A request large enough to run alone on the whole GPU (the persistent
+// single-graph kernel) rather than on one worker block.
+bool is_exclusive(const bm_server* s, const Request& r) {
+    return s->opt.exclusive_min_edges > 0 && r.nnz >= s->opt.exclusive_min_edges;
+}
+
+// Starts request r alone on the whole GPU: the workers are told to leave, and
+// the whole-GPU launch is queued behind them on the work stream, followed by
+// the copy of its control block and an event.  Returns BM_OK or an error.
+int32_t start_exclusive(bm_server* s, Request& r, int slot) {
+    size_t offs[kOffs];
+    request_bytes(r.nr, r.nc, r.nnz, true, offs);
+    unsigned char* b = s->pool + r.off;
+    bmd::Params p{};
+    p.nr = r.nr;
+    p.nc = r.nc;
+    p.col_ptr = (const int32_t*)(b + offs[0]);
+    p.row_idx = (const int32_t*)(b + offs[1]);
+    p.rmatch = (int32_t*)(b + offs[2]);
+    p.cmatch = (int32_t*)(b + offs[3]);
+    p.level = (int32_t*)(b + offs[4]);
+    p.root = (int32_t*)(b + offs[5]);
+    p.queue = (int2*)(b + offs[6]);
+    p.pred = (int32_t*)(b + offs[7]);
+    p.endpoints = (int32_t*)(b + offs[8]);
+    p.queue2 = (int2*)(b + offs[9]);
+    p.rvis = (int32_t*)(b + offs[10]);
+    p.crec = (int2*)(b + offs[11]);
+    p.ctl = (bmd::Ctl*)(b + offs[12]);
+    p.mode = s->opt.mode;
+    p.one_ep = 1;
+    __atomic_store_n(&s->head->stop, 1, __ATOMIC_RELEASE);  // workers finish what they hold and leave
+    int32_t rc = bmi::enqueue_match(p, r.nnz, s->opt.bfs == BM_GPUBFS_WR, r.greedy, s->work_stream);
+    if (rc != BM_OK) return rc;
+    if (cudaMemcpyAsync(&s->h_excl_ctl[slot], p.ctl, sizeof(bmd::Ctl), cudaMemcpyDeviceToHost, s->work_stream) !=
+            cudaSuccess ||
+        cudaEventRecord(s->excl_ev[slot], s->work_stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return BM_ERR_CUDA;
+    }
+    return BM_OK;
+}
+
 // One scheduling pass; called with s->mu held.  Returns whether anything moved.
 bool schedule_once(bm_server* s) {
     bool moved = false;
@@ -352,17 +423,55 @@ bool schedule_once(bm_server* s) {
         if (!s->opt.keep_results && r.has_mem) { s->alloc->release(r.off, r.bytes); r.has_mem = false; }
         moved = true;
     }
-    // uploads that finished, in order: publish
+    // requests running alone: finished, in launch order?
+    while (!s->excl_runs.empty()) {
+        const long long id = s->excl_runs.front().first;
+        const int slot = s->excl_runs.front().second;
+        const cudaError_t q = cudaEventQuery(s->excl_ev[slot]);
+        if (q == cudaErrorNotReady) break;
+        if (q != cudaSuccess) { (void)cudaGetLastError(); s->sticky = BM_ERR_CUDA; break; }
+        Request& r = s->reqs[id];
+        const bmd::Ctl& h = s->h_excl_ctl[slot];
+        r.card = h.card;
+        r.status = h.status != 0 ? h.status : h.err;
+        r.phases = h.phases;
+        r.state = DONE;
+        r.t_done = std::chrono::steady_clock::now();
+        s->inflight--;
+        s->completed++;
+        if (!s->opt.keep_results && r.has_mem) { s->alloc->release(r.off, r.bytes); r.has_mem = false; }
+        s->excl_runs.pop_front();
+        s->excl_free.push_back(slot);
+        moved = true;
+    }
+    // with no whole-GPU run queued the workers may run (again); starting one sets stop
+    if (s->excl_runs.empty()) __atomic_store_n(&s->head->stop, 0, __ATOMIC_RELEASE);
+    // uploads that finished, in order: publish to the workers, or run alone; a
+    // request for the workers waits until the whole-GPU runs ahead of it are done
     while (!s->uploading.empty()) {
         Request& r = s->reqs[s->uploading.front()];
         const cudaError_t q = cudaEventQuery(r.uploaded);
         if (q == cudaErrorNotReady) break;
         if (q != cudaSuccess) { s->sticky = BM_ERR_CUDA; break; }
+        if (is_exclusive(s, r)) {
+            if (s->excl_free.empty()) break;
+            const int slot = s->excl_free.back();
+            const int32_t rc = start_exclusive(s, r, slot);
+            if (rc != BM_OK) { s->sticky = rc; break; }
+            s->excl_free.pop_back();
+            s->excl_runs.emplace_back(r.id, slot);
+            r.state = RUNNING;
+            s->exclusive_runs++;
+            s->uploading.pop_front();
+            moved = true;
+            continue;
+        }
+        if (!s->excl_runs.empty()) break;
         const int slot = (int)(s->next_ticket % ring);
         if (s->ring_owner[slot] != -1) break;  // ticket next_ticket - ring still running
         const long long ticket = s->next_ticket++;
-        size_t offs[9];
-        request_bytes(r.nr, r.nc, r.nnz, offs);
+        size_t offs[kOffs];
+        request_bytes(r.nr, r.nc, r.nnz, false, offs);
         SlotDesc& d = s->desc[slot];
         d.id = r.id;
         d.nnz = r.nnz;
@@ -390,8 +499,8 @@ bool schedule_once(bm_server* s) {
         const long long id = s->pending.front();
         Request& r = s->reqs[id];
         if (r.state == CANCELLED) { s->pending.pop_front(); continue; }
-        size_t offs[9];
-        r.bytes = request_bytes(r.nr, r.nc, r.nnz, offs);
+        size_t offs[kOffs];
+        r.bytes = request_bytes(r.nr, r.nc, r.nnz, is_exclusive(s, r), offs);
         if (r.bytes > s->alloc->size()) {  // can never fit
             r.state = DONE;
             r.status = BM_ERR_TOO_LARGE;
@@ -418,10 +527,10 @@ bool schedule_once(bm_server* s) {
         s->pending.pop_front();
         moved = true;
     }
-    // workers: keep one launch alive while requests are published
+    // workers: keep one launch alive while requests are published (not while one runs alone)
     bool need = false;
     for (int k = 0; k < ring && !need; ++k) need = s->ring_owner[k] >= 0 && s->reqs[s->ring_owner[k]].state == RUNNING;
-    if (need) {
+    if (need && s->excl_runs.empty()) {
         const bool alive = s->worker_launched && cudaEventQuery(s->worker_ev) == cudaErrorNotReady;
         if (!alive) launch_workers(s);
     }
@@ -458,6 +567,7 @@ void bm_server_default_options(bm_server_options* o) {
     o->keep_results = 0;
     o->idle_timeout_ns = 50000000;  // 50 ms
     o->poll_interval_us = 5;
+    o->exclusive_min_edges = 1 << 18;
 }
 
 int32_t bm_server_create(const bm_server_options* opt, bm_server** out) {
@@ -467,7 +577,8 @@ int32_t bm_server_create(const bm_server_options* opt, bm_server** out) {
     if (opt) o = *opt; else bm_server_default_options(&o);
     if (o.ring_slots < 1 || o.ring_slots > (1 << 20) || o.block_size < 32 || o.block_size > 1024 ||
         o.block_size % 32 || o.blocks_per_sm < 1 || o.pool_bytes < 0 || o.reserve_bytes < 0 ||
-        o.idle_timeout_ns <= 0 || o.poll_interval_us < 0 || (o.mode != BM_APFB && o.mode != BM_APSB) ||
+        o.idle_timeout_ns <= 0 || o.poll_interval_us < 0 || o.exclusive_min_edges < 0 ||
+        (o.mode != BM_APFB && o.mode != BM_APSB) ||
         (o.bfs != BM_GPUBFS && o.bfs != BM_GPUBFS_WR))
         return BM_ERR_INVALID_ARG;
     bm_server* s = new (std::nothrow) bm_server();
@@ -512,11 +623,19 @@ int32_t bm_server_create(const bm_server_options* opt, bm_server** out) {
         cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->work_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->worker_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost((void**)&s->h_excl_ctl, sizeof(bmd::Ctl) * kExclSlots) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
         (void)cudaGetLastError();
         return fail(BM_ERR_CUDA);
     }
     s->d_busy = (int32_t*)(s->d_claimed + 1);
+    for (int k = 0; k < kExclSlots; ++k) {
+        if (cudaEventCreateWithFlags(&s->excl_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(BM_ERR_CUDA);
+        }
+        s->excl_free.push_back(kExclSlots - 1 - k);
+    }
     s->ring_owner.assign((size_t)o.ring_slots, -1);
     s->running = true;
     s->sched = std::thread(scheduler_main, s);
@@ -647,6 +766,7 @@ int32_t bm_server_get_stats(bm_server* s, bm_server_stats* st) {
     st->pool_used = (int64_t)s->alloc->used();
     st->grid = s->grid;
     st->block = s->block;
+    st->exclusive_runs = s->exclusive_runs;
     return s->sticky;
 }
 
@@ -662,6 +782,9 @@ int32_t bm_server_destroy(bm_server* s) {
     for (auto& kv : s->reqs)
         if (kv.second.uploaded) cudaEventDestroy(kv.second.uploaded);
     if (s->worker_ev) cudaEventDestroy(s->worker_ev);
+    for (int k = 0; k < kExclSlots; ++k)
+        if (s->excl_ev[k]) cudaEventDestroy(s->excl_ev[k]);
+    if (s->h_excl_ctl) cudaFreeHost(s->h_excl_ctl);
     if (s->work_stream) cudaStreamDestroy(s->work_stream);
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
     if (s->d_claimed) cudaFree(s->d_claimed);

@@ -17,6 +17,7 @@
 #include <mutex>
 
 #include "bm_device.cuh"
+#include "bm_internal.h"
 #include "bmatch.h"
 
 using bmd::Counters;
@@ -267,7 +268,9 @@ __global__ void k_fill(int32_t* a, long long n, int v) {
 // the result is maximal.  The scan looks at 4 rows per step with their loads
 // in flight together (hub columns can pass many taken rows).
 __global__ void k_greedy(int nc, const int32_t* __restrict__ cp, const int32_t* __restrict__ ri,
-                         int32_t* rm, int32_t* cm) {
+                         int32_t* rm, int32_t* cm, const Ctl* ctl = nullptr) {
+    // after an asynchronous CSR check on the same stream: an invalid CSR is not read
+    if (ctl && bmd::ld_volatile(&ctl->err) != 0) return;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
         if (cm[c] != -1) continue;
         const int end = __ldg(&cp[c + 1]);
@@ -1059,4 +1062,81 @@ extern "C" int32_t bm_match_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
     const int32_t status = h.status != 0 ? h.status : h.err;
     if (card_out) *card_out = h.card;
     return status;
+}
+
+// ------------------------------------------------------------------ internal: whole-GPU match of one graph
+namespace {
+struct ExclusiveDevice {
+    bool ready;
+    int grid[2];  // cooperative grid of k_match<false, true>, k_match<true, true>
+    int sms;
+};
+ExclusiveDevice g_excl_dev[kMaxDevices];
+std::mutex g_excl_mutex;
+}  // namespace
+
+int32_t bmi::enqueue_match(bmd::Params p, long long nnz, bool wr, int greedy, cudaStream_t st) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { (void)cudaGetLastError(); return BM_ERR_CUDA; }
+    if (dev < 0 || dev >= kMaxDevices) return BM_ERR_UNSUPPORTED;
+    ExclusiveDevice d;
+    {
+        std::lock_guard<std::mutex> lock(g_excl_mutex);
+        ExclusiveDevice& e = g_excl_dev[dev];
+        if (!e.ready) {
+            int sms = 0, coop = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return BM_ERR_CUDA;
+            }
+            if (!coop) return BM_ERR_UNSUPPORTED;
+            for (int w = 0; w < 2; ++w) {
+                int per_sm = 0;
+                const cudaError_t r =
+                    w ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true, true>, kDefaultBlock, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<false, true>, kDefaultBlock, 0);
+                if (r != cudaSuccess) { (void)cudaGetLastError(); return BM_ERR_CUDA; }
+                if (per_sm > 2048 / kDefaultBlock) per_sm = 2048 / kDefaultBlock;
+                while (per_sm > 1 && per_sm * sms > 2047) --per_sm;  // barrier words count blocks in 11 bits
+                if (per_sm < 1 || per_sm * sms > 2047) return BM_ERR_UNSUPPORTED;
+                e.grid[w] = per_sm * sms;
+            }
+            e.sms = sms;
+            e.ready = true;
+        }
+        d = e;
+    }
+    const int B = kDefaultBlock;
+    const int threads = 2048 / B * d.sms;
+    auto grid_of = [&](long long n) {
+        long long g = (n + B - 1) / B;
+        if (g > threads) g = threads;
+        return (int)(g < 1 ? 1 : g);
+    };
+    const size_t nr = (size_t)p.nr, nc = (size_t)p.nc;
+    if (cudaMemsetAsync(p.ctl, 0, sizeof(Ctl), st) != cudaSuccess) { (void)cudaGetLastError(); return BM_ERR_CUDA; }
+    k_check_csr<<<grid_of(nnz > p.nc ? nnz : (long long)p.nc + 1), B, 0, st>>>(p.nr, p.nc, nnz, p.col_ptr,
+                                                                               p.row_idx, p.ctl);
+    if ((nr && (cudaMemsetAsync(p.rmatch, 0xff, 4 * nr, st) != cudaSuccess ||
+                cudaMemsetAsync(p.rvis, 0, 4 * nr, st) != cudaSuccess)) ||
+        (nc && cudaMemsetAsync(p.cmatch, 0xff, 4 * nc, st) != cudaSuccess)) {
+        (void)cudaGetLastError();
+        return BM_ERR_CUDA;
+    }
+    if (greedy) k_greedy<<<grid_of(p.nc), B, 0, st>>>(p.nc, p.col_ptr, p.row_idx, p.rmatch, p.cmatch, p.ctl);
+    if (cudaGetLastError() != cudaSuccess) return BM_ERR_CUDA;
+    p.bfs_only = 0;
+    p.profile = nullptr;
+    p.profile_cap = 0;
+    p.max_phases = (p.nr < p.nc ? p.nr : p.nc) + 2;
+    p.phase_limit_is_error = 1;
+    p.stamp_base = 0;  // the stamps were just cleared
+    if (p.wait_ns <= 0) p.wait_ns = 5000000000LL;
+    if (p.total_ns <= 0) p.total_ns = 120000000000LL;
+    void* args[] = {&p};
+    const cudaError_t e = wr ? cudaLaunchCooperativeKernel((const void*)k_match<true, true>, d.grid[1], B, args, 0, st)
+                             : cudaLaunchCooperativeKernel((const void*)k_match<false, true>, d.grid[0], B, args, 0, st);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); return BM_ERR_CUDA; }
+    return BM_OK;
 }

@@ -162,3 +162,37 @@ def test_idle_workers_leave_and_come_back():
             srv.release(rid)
             time.sleep(0.05)  # longer than the idle timeout: the workers leave
         assert srv.stats()["worker_launches"] >= 2
+
+
+def test_large_requests_run_alone_on_the_whole_gpu():
+    """Requests with at least exclusive_min_edges edges run alone on the whole
+    GPU (the single-graph persistent kernel) while the others run on worker
+    blocks; mixed in one stream, every result is exact and valid.  A malformed
+    large request is reported as such and the requests behind it still run.
+    With the threshold at 0 every request stays on the workers."""
+    reqs = mixed_requests(24, seed=9)
+    want = [oracle.hopcroft_karp(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)[2] for g in reqs]
+    big = [g.nnz >= 20000 for g in reqs]
+    assert any(big) and not all(big)
+    bad_ri = reqs[0].row_idx.copy()
+    bad_ri[len(bad_ri) // 2] = reqs[0].n_rows  # one row id out of range
+    for threshold, expect_alone in ((20000, sum(big) * 2), (0, 0)):
+        with bmatch.Server(keep_results=1, pool_bytes=1 << 30, exclusive_min_edges=threshold) as srv:
+            ids = [srv.submit(g.n_rows, g.n_cols, g.col_ptr, g.row_idx) for g in reqs]
+            rid_bad = srv.submit(reqs[0].n_rows, reqs[0].n_cols, reqs[0].col_ptr, bad_ri)
+            ids += [srv.submit(g.n_rows, g.n_cols, g.col_ptr, g.row_idx) for g in reqs]
+            for k, rid in enumerate(ids):
+                g = reqs[k % len(reqs)]
+                info = srv.wait(rid)
+                assert info["state"] == bmatch.BM_REQ_DONE and info["status"] == 0, (k, info)
+                assert info["card"] == want[k % len(reqs)]
+                rm = np.empty(g.n_rows, np.int32)
+                cm = np.empty(g.n_cols, np.int32)
+                srv.fetch(rid, rm, cm)
+                assert_maximum(g, rm, cm, info["card"], want[k % len(reqs)])
+                srv.release(rid)
+            assert srv.wait(rid_bad)["status"] == bmatch.BM_ERR_INVALID_CSR
+            srv.release(rid_bad)
+            st = srv.stats()
+            assert st["exclusive_runs"] == expect_alone + (threshold > 0 and big[0])
+            assert st["pool_used"] == 0
