@@ -471,7 +471,12 @@ __device__ __forceinline__ void tile_load2(const Params& p, const int2* queue, i
 // p.rvis available): use_rv claims through the row stamps with `stamp` (see
 // the header comment); otherwise claims go to the column's level entry and,
 // with RV, the winner also stamps the row.
-template <bool WR, class PushCol, class PushEnd, bool NC = true, bool RV = false>
+// CA: the matched column of a row (rmatch) and the column's level are read
+// through L1.  Only for the grid-wide kernel, where every level starts after
+// the grid barrier's acquire (which makes these loads see the previous
+// levels' and phases' writes): within a level a matched row's column does not
+// change, and a stale "unvisited" level only costs a failed claim.
+template <bool WR, class PushCol, class PushEnd, bool NC = true, bool RV = false, bool CA = false>
 __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, bool direct, Smem& sm,
                                            Counters& cnt, PushCol push_col, PushEnd push_end, int stamp = 0,
                                            bool use_rv = false) {
@@ -504,15 +509,17 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
                 cm[u] = -3;
                 lv[u] = stamp;
                 if (own[u] >= 0) {
-                    cm[u] = __ldcg(&p.rmatch[r[u]]);
+                    cm[u] = CA ? __ldca(&p.rmatch[r[u]]) : __ldcg(&p.rmatch[r[u]]);
                     lv[u] = atomicMax(&p.rvis[r[u]], stamp);
                 }
             }
         } else {
 #pragma unroll
-            for (int u = 0; u < ILP; ++u) cm[u] = (own[u] >= 0) ? __ldcg(&p.rmatch[r[u]]) : -3;
+            for (int u = 0; u < ILP; ++u)
+                cm[u] = (own[u] >= 0) ? (CA ? __ldca(&p.rmatch[r[u]]) : __ldcg(&p.rmatch[r[u]])) : -3;
 #pragma unroll
-            for (int u = 0; u < ILP; ++u) lv[u] = (cm[u] >= 0 && !direct) ? __ldcg(&p.level[cm[u]]) : L0 - 1;
+            for (int u = 0; u < ILP; ++u)
+                lv[u] = (cm[u] >= 0 && !direct) ? (CA ? __ldca(&p.level[cm[u]]) : __ldcg(&p.level[cm[u]])) : L0 - 1;
         }
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
@@ -564,8 +571,10 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
 // whole grid.  New columns are appended at qe + (slot count), endpoints at
 // ep_phase (the phase's running count).  Frontiers of at most one tile per
 // block (the deep, narrow levels of long augmenting paths) take their tile
-// from blockIdx.x alone and claim columns by CAS without a test load.
-template <bool WR, bool RV = false>
+// from blockIdx.x alone and claim columns by CAS without a test load.  GRID:
+// called by the persistent kernel between grid barriers (L1 reads, see
+// tile_edges); the per-step kernels of the host-driven loop leave it off.
+template <bool WR, bool RV = false, bool GRID = false>
 __device__ __forceinline__ void step_expand(const Params& p, int2* queue, int qb, int qe, int lvl, int slot,
                                             Counters& cnt, Smem& sm, int stamp = 0) {
     const int q = qe - qb;
@@ -581,8 +590,9 @@ __device__ __forceinline__ void step_expand(const Params& p, int2* queue, int qb
     for (int tile = blockIdx.x; tile < ntiles;) {  // block-uniform
         tile_load<WR>(p, queue, qb, q, tile * tw, tw, sm, cnt, narrow ? nullptr : &p.ctl->tcnt[slot]);
         const int next_tile = narrow ? ntiles : sm.tile;
-        tile_edges<WR, decltype(push_col), decltype(push_end), true, RV>(p, tw, lvl, narrow, sm, cnt, push_col,
-                                                                          push_end, stamp, q <= RV_MAX_Q);
+        tile_edges<WR, decltype(push_col), decltype(push_end), true, RV, GRID>(p, tw, lvl, narrow, sm, cnt,
+                                                                                push_col, push_end, stamp,
+                                                                                q <= RV_MAX_Q);
         flush_block(p, queue, sm, qe, slot);
         tile = next_tile;
     }

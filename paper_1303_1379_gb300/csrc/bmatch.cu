@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
         for (;;) {
             const int s2 = step++;
             if (leader) { ctl->qcnt[(s2 + 1) % 3] = 0; ctl->ecnt[(s2 + 1) % 3] = 0; ctl->icnt[(s2 + 1) % 3] = 0; ctl->tcnt[(s2 + 1) % 3] = 0; }
-            step_expand<WR, RV>(p, qcur, qb, qe, lvl, s2 % 3, cnt, sm, p.stamp_base + phases);
+            step_expand<WR, RV, true>(p, qcur, qb, qe, lvl, s2 % 3, cnt, sm, p.stamp_base + phases);
             if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
             const int nq = sm.bc_a;           // columns inserted at this level
             const bool found = sm.bc_b > 0;   // some block claimed an endpoint
