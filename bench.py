@@ -44,6 +44,8 @@ WORKLOADS = {
               "removed, int32 CSR, greedy initial matching, seed 1",
     "stencil2000": "5-point stencil 2000x2000 (4M x 4M), 400,000 diagonals and 5% of off-diagonals "
                    "dropped, int32 CSR, greedy initial matching, seed 2",
+    "stencil500": "5-point stencil 500x500 (250k x 250k), 25,000 diagonals and 5% of off-diagonals "
+                  "dropped, int32 CSR, greedy initial matching, seed 2 (profiling size)",
     "uniform10k": "uniform 10,000 x 10,000, column degree U{1..8}, int32 CSR, empty initial "
                   "matching, seed 0",
 }

@@ -257,6 +257,8 @@ def workload(name: str) -> Graph:
         return rmat_graph(21, 1 << 25, seed=1)
     if name == "stencil2000":
         return stencil_graph(2000, 400_000, 0.05, seed=2)
+    if name == "stencil500":  # the same recipe on a 500 x 500 mesh (profiling runs)
+        return stencil_graph(500, 25_000, 0.05, seed=2)
     raise KeyError(name)
 
 
