@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-graphs", type=int, default=4096,
+                    help="graphs in the batched workload (smaller for profiling captures)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-distinct", type=int, default=48)
@@ -281,7 +283,7 @@ def bench_batched(args, torch, bmatch, stream, flush):
     import numpy as np
     from paper_1303_1379_gb300 import shard, synth
     t_gen = time.perf_counter()
-    b = synth.batch_graphs(4096, seed=3)
+    b = synth.batch_graphs(args.batch_graphs, seed=3)
     t_gen = time.perf_counter() - t_gen
     rank, world, _ = dist_env()
     G_all = b.n_graphs
@@ -345,7 +347,7 @@ def bench_batched(args, torch, bmatch, stream, flush):
         ok = shard.sum_over_ranks([0 if ok else 1], device=dev)[0] == 0
         G = G_all
     return {
-        "workload": BATCH_WORKLOAD, "graphs": G, "rows": R, "cols": C, "edges": E,
+        "workload": BATCH_WORKLOAD.replace("4,096", f"{G_all:,}", 1), "graphs": G, "rows": R, "cols": C, "edges": E,
         "generate_s": round(t_gen, 2),
         "ms": batch_ms, "graphs_per_s": G / (batch_ms * 1e-3),
         "gteps": E / (batch_ms * 1e-3) / 1e9,

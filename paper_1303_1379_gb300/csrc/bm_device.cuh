@@ -758,35 +758,49 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
         if (m != -1 && (m < 0 || m >= nc || __ldcg(&p.cmatch[m]) != r)) __stcg(&p.rmatch[r], -1);
     }
     __syncthreads();
-    // ---- cheap matching (Section 4): unmatched columns claim their first free row;
-    // first tries of 4 columns per thread in flight, then the rest of each list
+    // ---- cheap matching (Section 4): unmatched columns claim their first free row.
+    // A thread walks the lists of 4 columns together, GW rows of each per step,
+    // so that 4 x GW row loads and then 4 x GW match loads are in flight at once
+    // and a thread takes as long as its longest walk / GW (not the sum of its walks).
     if (greedy) {
+        constexpr int GW = 4;
         for (int base = 0; base < nc; base += 4 * T) {
-            int c[4], b[4], e[4], r0[4];
+            int c[4], pos[4], e[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 c[u] = base + u * T + t;
-                b[u] = e[u] = 0;
+                pos[u] = e[u] = 0;
                 if (c[u] < nc && __ldcg(&p.cmatch[c[u]]) == -1) {
-                    b[u] = ld_csr<NC>(&p.col_ptr[c[u]]);
+                    pos[u] = ld_csr<NC>(&p.col_ptr[c[u]]);
                     e[u] = ld_csr<NC>(&p.col_ptr[c[u] + 1]);
                 }
             }
+            for (;;) {
+                int r[4][GW], m[4][GW];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) r0[u] = b[u] < e[u] ? ld_csr<NC>(&p.row_idx[b[u]]) : -1;
+                for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (b[u] >= e[u]) continue;
-                int pos = b[u];
-                int r = r0[u];
-                for (;;) {
-                    if (ld_volatile(&p.rmatch[r]) == -1 && atomicCAS(&p.rmatch[r], -1, c[u]) == -1) {
-                        p.cmatch[c[u]] = r;
-                        break;
+                    for (int k = 0; k < GW; ++k) r[u][k] = pos[u] + k < e[u] ? ld_csr<NC>(&p.row_idx[pos[u] + k]) : -1;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int k = 0; k < GW; ++k) m[u][k] = r[u][k] >= 0 ? ld_volatile(&p.rmatch[r[u][k]]) : 0;
+                bool more = false;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (pos[u] >= e[u]) continue;
+                    bool got = false;
+#pragma unroll
+                    for (int k = 0; k < GW; ++k) {  // the first free row of the window, in list order
+                        if (!got && m[u][k] == -1 && atomicCAS(&p.rmatch[r[u][k]], -1, c[u]) == -1) {
+                            p.cmatch[c[u]] = r[u][k];
+                            got = true;
+                        }
                     }
-                    if (++pos >= e[u]) break;
-                    r = ld_csr<NC>(&p.row_idx[pos]);
+                    pos[u] = got ? e[u] : pos[u] + GW;
+                    more |= pos[u] < e[u];
                 }
+                if (!more) break;
             }
         }
     }
