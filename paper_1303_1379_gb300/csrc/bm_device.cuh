@@ -400,7 +400,7 @@ __device__ __forceinline__ void step_next_roots(const Params& p, const int2* q, 
 // takes the next tile index from it (into sm.tile).  Ends with __syncthreads.
 template <bool WR, bool NC = true>
 __device__ __forceinline__ void tile_load(const Params& p, const int2* queue, int qb, int q, int first, int tw,
-                                          Smem& sm, Counters& cnt, int32_t* tile_ctr) {
+                                          Smem& sm, Counters& cnt, int32_t* tile_ctr, int grab = 1, int ctr_base = -1) {
     const int t = threadIdx.x;
     const int i = first + t;
     int c = -1, beg = 0, deg = 0, myroot = -1, rlev = L0;
@@ -412,7 +412,7 @@ __device__ __forceinline__ void tile_load(const Params& p, const int2* queue, in
         deg = ld_csr<NC>(&p.col_ptr[c + 1]) - beg;
         if (WR) rlev = __ldcg(&p.level[myroot]);
     }
-    if (t == 0 && tile_ctr) sm.tile = gridDim.x + atomicAdd(tile_ctr, 1);
+    if (t == 0 && tile_ctr) sm.tile = (ctr_base < 0 ? (int)gridDim.x : ctr_base) + atomicAdd(tile_ctr, grab);
     const int off = block_exclusive_scan(deg, sm);
     if (WR && rlev < L0 - 1) c = -1;  // Algorithm 4: root already served
     if (c >= 0) cnt.cols++;
@@ -587,6 +587,31 @@ __device__ __forceinline__ void step_expand(const Params& p, int2* queue, int qb
     const bool narrow = ntiles <= (int)gridDim.x;
     auto push_col = [&](int2 v) { push_block(p, queue, sm, qe, slot, v); };
     auto push_end = [&](int v) { push(p.endpoints, 0, &p.ctl->ep_phase, v); };
+    if (GRID && !narrow) {
+        // Guided self-scheduling of a wide level: block b first takes columns
+        // [b w0, (b + 1) w0) with w0 ~ q / 2G, then ranges from a position
+        // counter, each about 1/2G of what is left past its current range (32
+        // to blockDim columns), prefetched while it works on the current one:
+        // large ranges first, small ones at the end, so that no block is left
+        // with a heavy 512-column tile when the others are done.
+        const int G = gridDim.x, T = blockDim.x;
+        auto clamp_w = [&](long long w) { return (int)min((long long)T, max(32LL, (w + 31) & ~31LL)); };
+        const int w0 = clamp_w(((long long)q + 2 * G - 1) / (2 * G));
+        int first = (int)min((long long)blockIdx.x * w0, (long long)q);
+        int width = w0;
+        while (first < q) {  // block-uniform
+            const int grab = clamp_w(((long long)q - first - width) / (2 * G));
+            tile_load<WR>(p, queue, qb, q, first, width, sm, cnt, &p.ctl->tcnt[slot], grab, G * w0);
+            const int next_first = sm.tile;
+            tile_edges<WR, decltype(push_col), decltype(push_end), true, RV, GRID>(p, width, lvl, false, sm, cnt,
+                                                                                    push_col, push_end, stamp,
+                                                                                    q <= RV_MAX_Q);
+            flush_block(p, queue, sm, qe, slot);
+            first = next_first;
+            width = grab;
+        }
+        return;
+    }
     for (int tile = blockIdx.x; tile < ntiles;) {  // block-uniform
         tile_load<WR>(p, queue, qb, q, tile * tw, tw, sm, cnt, narrow ? nullptr : &p.ctl->tcnt[slot]);
         const int next_tile = narrow ? ntiles : sm.tile;
