@@ -30,6 +30,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -87,18 +88,26 @@ def dist_env():
     return rank, world, local
 
 
+def _code_only(text: str) -> str:
+    """C++/CUDA source without comments and with whitespace collapsed, so that
+    editing a comment does not count as changing the kernel."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_hash() -> str:
-    """Hash of the sources that make up the persistent matching kernel: the
+    """Hash of the code that makes up the persistent matching kernel: the
     device header and the k_match kernel body (other kernels in the same file
-    do not change it)."""
+    do not change it), comments and whitespace excluded."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1303_1379_gb300/csrc/bm_device.cuh"), "rb") as fh:
-        h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_1303_1379_gb300/csrc/bm_device.cuh"), "r") as fh:
+        h.update(_code_only(fh.read()).encode())
     with open(os.path.join(ROOT, "paper_1303_1379_gb300/csrc/bmatch.cu"), "r") as fh:
         text = fh.read()
     start = text.find("// One launch per match")
     end = text.find("// ---- per-step kernels")
-    h.update(text[start:end].encode())
+    h.update(_code_only(text[start:end]).encode())
     return h.hexdigest()[:16]
 
 

@@ -397,7 +397,10 @@ __device__ __forceinline__ void step_next_roots(const Params& p, const int2* q, 
 // served) are two independent loads whose latency overlaps the prefix sum; a
 // column whose root is served keeps its place in the prefix sum but gets
 // sm.col = -1 and its edges are skipped.  If tile_ctr is given, thread 0 also
-// takes the next tile index from it (into sm.tile).  Ends with __syncthreads.
+// takes the block's next work item from it: sm.tile = ctr_base + the counter's
+// old value, after adding `grab` (a tile index with grab 1 and ctr_base
+// gridDim.x; a queue position with a range width and the end of the static
+// ranges in the guided schedule).  Ends with __syncthreads.
 template <bool WR, bool NC = true>
 __device__ __forceinline__ void tile_load(const Params& p, const int2* queue, int qb, int q, int first, int tw,
                                           Smem& sm, Counters& cnt, int32_t* tile_ctr, int grab = 1, int ctr_base = -1) {
