@@ -1,5 +1,5 @@
 """Shared test helpers: move a synthetic graph to the GPU, run the CUDA path
-through the C-ABI binding, and judge its output with the oracle."""
+through the C-ABI binding, and check its output against the oracle."""
 from __future__ import annotations
 
 import numpy as np
