@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(1024, 1) k_batch(BatchParams bp) {
         p.one_ep = bp.one_ep;
         int card = 0, phases = 0;
         long long levels = 0, eps = 0;
-        const int st = bmd::block_match_graph<WR, true>(p, bp.greedy, sm, cnt, card, phases, levels, eps);
+        const int st = bmd::block_match_graph<WR, true, true>(p, bp.greedy, sm, cnt, card, phases, levels, eps);
         if (threadIdx.x == 0) {
             bp.card_out[g] = card;
             bp.status_out[g] = st;

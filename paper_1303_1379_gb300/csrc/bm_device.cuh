@@ -772,7 +772,13 @@ __device__ __forceinline__ void block_full_init(const Params& p, Smem& sm, Count
 // search visited and keeps the roots that are still unmatched (work per phase
 // proportional to the search, not to n_cols).  The other modes run the full
 // passes.  Returns the graph's status.
-template <bool WR, bool NC>
+// CA: the tile expansion reads rows' matches and columns' levels through L1.
+// Only when no other block writes the graph's arrays during the launch and the
+// memory is not reused for another graph within it (the batched kernel: the
+// block's own writes and atomics keep its SM's L1 coherent, and every launch
+// starts with a clean L1); the serving workers recycle pool memory within one
+// launch and read through L2.
+template <bool WR, bool NC, bool CA = false>
 __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters& cnt, int& card_out,
                                  int& phases_out, long long& levels_out, long long& eps_out) {
     const int T = blockDim.x;
@@ -857,7 +863,7 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
             for (int first = 0; first < q; first += tw) {
                 if (wide) tile_load2<WR, NC>(p, p.queue, qb, q, first, sm, cnt);
                 else tile_load<WR, NC>(p, p.queue, qb, q, first, T, sm, cnt, nullptr);
-                tile_edges<WR, decltype(push_col), decltype(push_end), NC>(p, tw, lvl, q <= T, sm, cnt,
+                tile_edges<WR, decltype(push_col), decltype(push_end), NC, false, CA>(p, tw, lvl, q <= T, sm, cnt,
                                                                            push_col, push_end);
                 __syncthreads();  // sm.off/beg/col/root are reused by the next tile
             }
