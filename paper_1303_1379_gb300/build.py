@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libbmatch.so")
 SOURCES = [os.path.join(CSRC, f) for f in ("bmatch.cu", "bm_batch.cu", "bm_server.cu")]
-DEPENDS = SOURCES + [os.path.join(CSRC, "bm_device.cuh"), os.path.join(INCLUDE, "bmatch.h")]
+DEPENDS = SOURCES + [os.path.join(CSRC, f) for f in ("bm_device.cuh", "bm_internal.h", "bm_pool.h")] + \
+    [os.path.join(INCLUDE, "bmatch.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

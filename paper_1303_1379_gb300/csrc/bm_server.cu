@@ -35,11 +35,13 @@
 
 #include "bm_device.cuh"
 #include "bm_internal.h"
+#include "bm_pool.h"
 #include "bmatch.h"
 
 using bmd::Counters;
 using bmd::Params;
 using bmd::Smem;
+using bms::PoolAllocator;
 
 namespace {
 
@@ -196,51 +198,6 @@ __global__ void __launch_bounds__(1024, 1) k_serve(ServeParams sp) {
     }
 }
 
-// First-fit allocator over [0, size) in 256-byte units, coalescing on free.
-class PoolAllocator {
-  public:
-    explicit PoolAllocator(size_t size) : size_(size & ~size_t(255)) {
-        if (size_) free_[0] = size_;
-    }
-    bool alloc(size_t bytes, size_t* off) {
-        bytes = (bytes + 255) & ~size_t(255);
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                *off = it->first;
-                const size_t rest = it->second - bytes, at = it->first + bytes;
-                free_.erase(it);
-                if (rest) free_[at] = rest;
-                used_ += bytes;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes) {
-        bytes = (bytes + 255) & ~size_t(255);
-        used_ -= bytes;
-        auto it = free_.emplace(off, bytes).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-    size_t size() const { return size_; }
-    size_t used() const { return used_; }
-
-  private:
-    size_t size_;
-    size_t used_ = 0;
-    std::map<size_t, size_t> free_;
-};
 
 enum ReqState { PENDING = 0, UPLOADING = 1, RUNNING = 2, DONE = 3, CANCELLED = 4 };
 
