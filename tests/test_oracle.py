@@ -291,3 +291,21 @@ def test_random_permutation_keeps_the_maximum():
         assert a == b
     p = synth.permutation(1000, 5, 0)
     assert sorted(p.tolist()) == list(range(1000)) and not np.array_equal(p, np.arange(1000))
+
+
+def test_batch_recipe():
+    """The batched workload's recipe: rows log-uniform in [100, 50,000], columns
+    = rows x U[0.8, 1.25], column degrees in 1..round(2mu - 1) <= 23, every
+    graph a valid CSR at its offsets, and the same batch for the same seed."""
+    b = synth.batch_graphs(96, seed=3)
+    b2 = synth.batch_graphs(96, seed=3)
+    assert np.array_equal(b.row_idx, b2.row_idx) and np.array_equal(b.col_ptr, b2.col_ptr)
+    assert b.n_rows.min() >= 100 and b.n_rows.max() <= 50_000
+    ratio = b.n_cols / b.n_rows
+    assert ratio.min() >= 0.8 - 1e-2 and ratio.max() <= 1.25 + 1e-2
+    assert np.array_equal(np.diff(b.row_off), b.n_rows) and np.array_equal(np.diff(b.col_off), b.n_cols)
+    for k in range(b.n_graphs):
+        g = b.graph(k)
+        assert oracle.csr_check(g.n_rows, g.n_cols, g.col_ptr, g.row_idx) == 0
+        deg = np.diff(g.col_ptr)
+        assert deg.min() >= 1 and deg.max() <= 23
