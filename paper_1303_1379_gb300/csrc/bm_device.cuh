@@ -576,7 +576,9 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
 // block (the deep, narrow levels of long augmenting paths) take their tile
 // from blockIdx.x alone and claim columns by CAS without a test load.  GRID:
 // called by the persistent kernel between grid barriers (L1 reads, see
-// tile_edges); the per-step kernels of the host-driven loop leave it off.
+// tile_edges; wider levels are handed out in guided ranges, below); the
+// per-step kernels of the host-driven loop leave it off and take fixed tiles
+// from the step's tile counter.
 template <bool WR, bool RV = false, bool GRID = false>
 __device__ __forceinline__ void step_expand(const Params& p, int2* queue, int qb, int qe, int lvl, int slot,
                                             Counters& cnt, Smem& sm, int stamp = 0) {
