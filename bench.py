@@ -161,14 +161,31 @@ def algorithmic_bytes(st: dict, nr: int, nc: int, wr: bool) -> int:
     return int(init + frontier + edges + ins + ends + alt + fix)
 
 
+def nvsmi_gpu_id(torch, device_index: int) -> str:
+    """The id under which nvidia-smi knows the GPU that torch calls
+    `device_index`.  nvidia-smi ignores CUDA_VISIBLE_DEVICES and numbers GPUs
+    physically, so a logical index could name another job's GPU: use the
+    device's UUID, else map the index through CUDA_VISIBLE_DEVICES."""
+    try:
+        u = str(torch.cuda.get_device_properties(device_index).uuid)
+        if u:
+            return u if u.startswith(("GPU-", "MIG-")) else "GPU-" + u
+    except Exception:
+        pass
+    vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    if device_index < len(vis):
+        return vis[device_index]
+    return str(device_index)
+
+
 class ClockSampler:
     """nvidia-smi SM clock and throttle reasons, sampled every 200 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
         self.proc = None
         self.lines = []
         self.thread = None
@@ -216,7 +233,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "gpu": self.gpu}
 
 
 def load_workload(name):
@@ -524,7 +541,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(torch.cuda.current_device() if world == 1 else local)
+    clocks = ClockSampler(nvsmi_gpu_id(torch, torch.cuda.current_device()))
     clocks.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]

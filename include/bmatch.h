@@ -397,18 +397,26 @@ BM_API int32_t bm_server_destroy(bm_server *s);
  *                     return.  Caller-owned.
  *   stream            cudaStream_t for all work (NULL = legacy default stream).
  *   card_out          host, nullable: |M|.
- * Size limit: 512 + 4*(4*n_cols + 2*n_rows) bytes (each array rounded up to
- * 256 bytes) must fit in BM_NOALLOC_SCRATCH_BYTES, else BM_ERR_TOO_LARGE is
- * returned before any GPU work.  Invalid CSR or matching: BM_ERR_INVALID_CSR /
+ * Size limit: 1024 bytes of control block plus five arrays, each rounded up
+ * to a multiple of 256 bytes -- 4*n_cols (levels), 4*n_cols (roots),
+ * 4*n_rows (predecessors), 8*n_cols (queue), 4*n_rows (endpoints) -- must fit
+ * in BM_NOALLOC_SCRATCH_BYTES (about 1024 + 4*(4*n_cols + 2*n_rows); square
+ * graphs up to n = 1,398,016), else BM_ERR_TOO_LARGE is returned before any
+ * GPU work.  Invalid CSR or matching: BM_ERR_INVALID_CSR /
  * BM_ERR_INVALID_MATCHING (rmatch/cmatch unchanged then).
- * The first call on a device finds the scratch array's device address
- * (cudaGetSymbolAddress) and the launch size; make that first call before any
- * stream capture.  Calls never allocate (no cudaMalloc, cudaFree or library
- * routine that allocates) and return after the work finished.  All calls share
- * the one scratch array, which keeps the previous call's contents (the parts
- * that must start at zero are cleared by each call): calls that overlap on the
- * GPU -- concurrent calls on different streams or host threads -- race and
- * must be serialised by the caller.
+ * The call is synchronous: it returns after the work finished, reading the
+ * result through a pageable host copy and a stream synchronisation, so it
+ * cannot be captured in a CUDA graph and must not be called while a stream
+ * capture is active.  The first call on a device finds the scratch array's
+ * device address (cudaGetSymbolAddress) and the launch size, and keeps them
+ * for the life of the process: do not use this entry point across a
+ * cudaDeviceReset.  The 32 MiB are reserved on each device when the library's
+ * device code is loaded there, which with lazy module loading may be the first
+ * call; calls allocate nothing (no cudaMalloc, cudaFree or library routine
+ * that allocates).  All calls share the one scratch array, which keeps the
+ * previous call's contents (the parts that must start at zero are cleared by
+ * each call): calls that overlap on the GPU -- concurrent calls on different
+ * streams or host threads -- race and must be serialised by the caller.
  */
 #define BM_NOALLOC_SCRATCH_BYTES (32u << 20)
 BM_API int32_t bm_match_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,

@@ -954,6 +954,11 @@ std::mutex g_noalloc_mutex;
 
 size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// The control block's share of the scratch array: a fixed size, so that the
+// size limit stated in bmatch.h does not move when the control block grows.
+constexpr size_t kNoallocCtlBytes = 1024;
+static_assert(sizeof(Ctl) <= kNoallocCtlBytes, "control block outgrew its share of the scratch array");
+
 // Once per device, with that device current: the host-side name of the array
 // is not a device address, so look the address up and keep it.
 int32_t noalloc_setup(int dev, NoallocDevice* out) {
@@ -994,7 +999,7 @@ extern "C" int32_t bm_match_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
     if (!col_ptr || (!row_idx && nnz > 0) || (!rmatch && n_rows > 0) || (!cmatch && n_cols > 0))
         return BM_ERR_INVALID_ARG;
     const size_t nr = (size_t)n_rows, nc = (size_t)n_cols;
-    const size_t off_lv = round256(sizeof(Ctl));
+    const size_t off_lv = kNoallocCtlBytes;
     const size_t off_rt = off_lv + round256(4 * nc);
     const size_t off_pd = off_rt + round256(4 * nc);
     const size_t off_q = off_pd + round256(4 * nr);

@@ -173,6 +173,54 @@ def test_block_diagonal_batch_is_sum_of_blocks():
     assert card == int(cards.sum())
 
 
+# ------------------------------------------------------------ CSR check
+def test_csr_check_rejects_each_kind_of_bad_csr():
+    """The CSR of Section 3 (cxadj / cadj): col_ptr starts at 0, never
+    decreases and ends at nnz; every row id lies in [0, n_rows).  Each bad
+    case below breaks exactly one of these rules and keeps the others, so
+    that dropping any one test in orc_csr_check lets a case through."""
+    BAD_ARG, BAD_INDEX = -1, -3
+    # 3 rows, 3 columns, 4 edges: c0 {0, 2}, c1 {}, c2 {1, 2}
+    cp = np.array([0, 2, 2, 4], np.int32)
+    ri = np.array([0, 2, 1, 2], np.int32)
+    assert oracle.csr_check(3, 3, cp, ri) == 0
+    assert oracle.csr_check(3, 0, np.array([0], np.int32), np.zeros(0, np.int32)) == 0  # no columns
+    assert oracle.csr_check(0, 2, np.array([0, 0, 0], np.int32), np.zeros(0, np.int32)) == 0  # no rows, no edges
+    # col_ptr[0] != 0 (the rest still monotone and ending at nnz)
+    assert oracle.csr_check(3, 3, np.array([1, 2, 2, 4], np.int32), ri) == BAD_ARG
+    # col_ptr decreases once, starts at 0 and ends at nnz
+    assert oracle.csr_check(3, 3, np.array([0, 3, 2, 4], np.int32), ri) == BAD_ARG
+    assert oracle.csr_check(3, 3, np.array([0, 2, 4, 4], np.int32), ri) == 0  # same values, monotone: fine
+    # col_ptr[nc] != nnz, above and below (monotone, from 0)
+    assert oracle.csr_check(3, 3, np.array([0, 2, 2, 5], np.int32), ri) == BAD_ARG
+    assert oracle.csr_check(3, 3, np.array([0, 2, 2, 3], np.int32), ri) == BAD_ARG
+    # a row id out of range: one past the end, negative, far out
+    for bad in (3, -1, 1 << 30):
+        r2 = ri.copy()
+        r2[3] = bad
+        assert oracle.csr_check(3, 3, cp, r2) == BAD_INDEX
+    r2 = ri.copy()
+    r2[0] = 3  # the first edge too
+    assert oracle.csr_check(3, 3, cp, r2) == BAD_INDEX
+    # the bound is the row count: row 2 is out of range for 2 rows
+    assert oracle.csr_check(2, 3, cp, ri) == BAD_INDEX
+    # negative sizes
+    assert oracle.csr_check(-1, 3, cp, ri) == BAD_ARG
+    assert oracle.csr_check(3, -1, np.array([0], np.int32), ri) == BAD_ARG
+    # a real generator's output stays valid; one corrupted entry anywhere is caught
+    g = synth.uniform_graph(300, 250, 6, seed=12)
+    assert oracle.csr_check(g.n_rows, g.n_cols, g.col_ptr, g.row_idx) == 0
+    rng = np.random.default_rng(12)
+    for _ in range(20):
+        r2 = g.row_idx.copy()
+        r2[int(rng.integers(g.nnz))] = int(rng.choice([-2, g.n_rows, g.n_rows + 7]))
+        assert oracle.csr_check(g.n_rows, g.n_cols, g.col_ptr, r2) == BAD_INDEX
+        c2 = g.col_ptr.copy()
+        k = int(rng.integers(1, g.n_cols))
+        c2[k] = c2[k + 1] + 1  # one entry above its successor
+        assert oracle.csr_check(g.n_rows, g.n_cols, c2, g.row_idx) == BAD_ARG
+
+
 # ------------------------------------------------------------ certificate, validation
 def test_konig_rejects_non_maximum_and_invalid():
     # path r0 - c0 - r1 - c1 : greedy takes (r0,c0), (r1,c1) => maximum 2.

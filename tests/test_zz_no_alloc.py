@@ -55,15 +55,40 @@ def test_noalloc_agrees_with_bm_match_on_consecutive_calls():
         assert_maximum(g, rm, cm, card, want)
 
 
-def test_noalloc_rejects_graphs_beyond_its_scratch():
-    n = 4_000_000  # needs 4*(3n + 2n) bytes > 32 MiB
-    cp = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+def scratch_need(n_rows, n_cols):
+    """Bytes of scratch a graph needs, as bmatch.h states the limit: 1024 bytes
+    of control block plus levels, roots and queue over the columns (4, 4 and 8
+    bytes each) and predecessors and endpoints over the rows (4 bytes each),
+    each array rounded up to 256 bytes."""
+    r = lambda b: (b + 255) // 256 * 256
+    return 1024 + 2 * r(4 * n_cols) + r(8 * n_cols) + 2 * r(4 * n_rows)
+
+
+def empty_graph_call(n_rows, n_cols):
+    cp = torch.zeros(n_cols + 1, dtype=torch.int32, device="cuda")
     ri = torch.zeros(1, dtype=torch.int32, device="cuda")
-    rm = torch.full((n,), -1, dtype=torch.int32, device="cuda")
-    cm = torch.full((n,), -1, dtype=torch.int32, device="cuda")
-    rc, _ = bmatch.bm_match_noalloc(n, n, 0, cp, ri, rm, cm)
+    rm = torch.full((n_rows,), -1, dtype=torch.int32, device="cuda")
+    cm = torch.full((n_cols,), -1, dtype=torch.int32, device="cuda")
+    return bmatch.bm_match_noalloc(n_rows, n_cols, 0, cp, ri, rm, cm)
+
+
+def test_noalloc_rejects_graphs_beyond_its_scratch():
+    limit = 32 << 20
+    n = 4_000_000  # needs about 1024 + 4*(4n + 2n) bytes, far above 32 MiB
+    assert scratch_need(n, n) > limit
+    rc, _ = empty_graph_call(n, n)
     assert rc == bmatch.BM_ERR_TOO_LARGE
     assert bmatch.status_string(rc) != "unknown status"
+    # the boundary: the largest square graph that fits runs, one more row and column does not
+    n = 1_398_016
+    assert scratch_need(n, n) <= limit < scratch_need(n + 1, n + 1)
+    rc, card = empty_graph_call(n, n)
+    assert rc == bmatch.BM_OK and card == 0
+    rc, _ = empty_graph_call(n + 1, n + 1)
+    assert rc == bmatch.BM_ERR_TOO_LARGE
+    # rectangular: the rows' share and the columns' share are counted separately
+    rc, _ = empty_graph_call(2 * n, n // 2)
+    assert (rc == bmatch.BM_OK) == (scratch_need(2 * n, n // 2) <= limit)
 
 
 def test_noalloc_rejects_invalid_matching_and_leaves_it_unchanged():
