@@ -110,7 +110,9 @@ typedef struct bm_stats {
     int64_t edges_to_matched;  /* scanned edges whose row was matched                       */
     int64_t alternate_steps;   /* columns rematched by Alternate                             */
     int64_t kernel_ns;         /* device time of the persistent launch (0 for the host loop) */
-    int64_t reserved[2];
+    int32_t grid, block;       /* blocks and threads per block of the persistent launch
+                                  (0, 0 for the host loop)                                   */
+    int64_t roots;             /* search roots (unmatched columns with rows) over all phases  */
 } bm_stats;
 
 typedef struct bm_ctx bm_ctx;
@@ -251,7 +253,9 @@ typedef struct bm_batch_stats {
     int32_t reserved0;
     int64_t phases, levels, columns_expanded, edges_scanned, endpoints, fix_repairs,
             alternate_steps;   /* sums over the graphs                                     */
-    int64_t reserved[4];
+    int64_t edges_to_matched;  /* scanned edges whose row was matched (sum over graphs)    */
+    int64_t inserted;          /* columns the BFS added to a level (sum over graphs)       */
+    int64_t reserved[2];
 } bm_batch_stats;
 
 typedef struct bm_batch bm_batch;

@@ -73,7 +73,8 @@ class bm_batch_stats(ctypes.Structure):
                 ("levels", ctypes.c_int64), ("columns_expanded", ctypes.c_int64),
                 ("edges_scanned", ctypes.c_int64), ("endpoints", ctypes.c_int64),
                 ("fix_repairs", ctypes.c_int64), ("alternate_steps", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 4)]
+                ("edges_to_matched", ctypes.c_int64), ("inserted", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 2)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -104,7 +105,8 @@ class bm_stats(ctypes.Structure):
                 ("endpoints", ctypes.c_int64), ("fix_repairs", ctypes.c_int64),
                 ("inserted", ctypes.c_int64), ("edges_to_matched", ctypes.c_int64),
                 ("alternate_steps", ctypes.c_int64), ("kernel_ns", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 2)]
+                ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("roots", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

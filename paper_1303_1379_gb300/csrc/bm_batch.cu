@@ -32,7 +32,7 @@ struct alignas(128) BatchCtl {
     int32_t next;        // next position in the largest-first order
     int32_t err;         // first error of any graph
     int32_t pad[30];
-    long long phases, levels, cols, edges, endpoints, fixes, em, alt;
+    long long phases, levels, cols, edges, endpoints, fixes, em, alt, ins;
 };
 
 struct BatchParams {
@@ -65,7 +65,7 @@ template <bool WR>
 __global__ void __launch_bounds__(1024, 1) k_batch(BatchParams bp) {
     __shared__ Smem sm;
     Counters cnt{0, 0, 0, 0, 0};
-    long long lv_all = 0, ep_all = 0, ph_all = 0;
+    long long lv_all = 0, ep_all = 0, ph_all = 0, ins_all = 0;
     for (;;) {
         if (threadIdx.x == 0) sm.tile = atomicAdd(&bp.ctl->next, 1);
         __syncthreads();
@@ -88,8 +88,8 @@ __global__ void __launch_bounds__(1024, 1) k_batch(BatchParams bp) {
         p.mode = bp.mode;
         p.one_ep = bp.one_ep;
         int card = 0, phases = 0;
-        long long levels = 0, eps = 0;
-        const int st = bmd::block_match_graph<WR, true, true>(p, bp.greedy, sm, cnt, card, phases, levels, eps);
+        long long levels = 0, eps = 0, ins = 0;
+        const int st = bmd::block_match_graph<WR, true, true>(p, bp.greedy, sm, cnt, card, phases, levels, eps, ins);
         if (threadIdx.x == 0) {
             bp.card_out[g] = card;
             bp.status_out[g] = st;
@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(1024, 1) k_batch(BatchParams bp) {
             lv_all += levels;
             ep_all += eps;
             ph_all += phases;
+            ins_all += ins;
         }
         __syncthreads();  // sm.tile / sm.ok are rewritten for the next graph
     }
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(1024, 1) k_batch(BatchParams bp) {
         atomicAdd((unsigned long long*)&bp.ctl->levels, (unsigned long long)lv_all);
         atomicAdd((unsigned long long*)&bp.ctl->endpoints, (unsigned long long)ep_all);
         atomicAdd((unsigned long long*)&bp.ctl->phases, (unsigned long long)ph_all);
+        atomicAdd((unsigned long long*)&bp.ctl->ins, (unsigned long long)ins_all);
     }
 }
 
@@ -402,6 +404,8 @@ int32_t bm_batch_match(bm_batch* b, int32_t greedy, int32_t* rmatch, int32_t* cm
         stats->endpoints = h.endpoints;
         stats->fix_repairs = h.fixes;
         stats->alternate_steps = h.alt;
+        stats->edges_to_matched = h.em;
+        stats->inserted = h.ins;
         stats->grid = b->grid;
         stats->block = b->block;
     }

@@ -73,9 +73,10 @@ struct alignas(128) Ctl {
     int32_t status;            // final status of the launch
     int32_t card;              // |M| at the end
     int32_t initial_card;
-    int32_t phases;
+    int32_t phases;            // outer iterations of Algorithm 1, the last (empty) one included
     int32_t n_endpoints_last;  // endpoints of the last BFS (inspection)
-    int32_t pad1[11];
+    int32_t searches;          // breadth-first searches run (entries of the phase profile)
+    int32_t pad1[10];
     long long levels;
     long long max_levels;
     long long cols_expanded;
@@ -86,6 +87,7 @@ struct alignas(128) Ctl {
     long long edges_matched;   // visited edges whose row was matched
     long long alt_steps;       // Alternate steps (columns rematched)
     long long kernel_ns;       // duration of the persistent launch (%globaltimer)
+    long long roots;           // search roots over all phases
 };
 
 struct Params {
@@ -782,7 +784,8 @@ __device__ __forceinline__ void block_full_init(const Params& p, Smem& sm, Count
 // launch and read through L2.
 template <bool WR, bool NC, bool CA = false>
 __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters& cnt, int& card_out,
-                                 int& phases_out, long long& levels_out, long long& eps_out) {
+                                 int& phases_out, long long& levels_out, long long& eps_out,
+                                 long long& ins_out) {
     const int T = blockDim.x;
     const int t = threadIdx.x;
     const int nr = p.nr, nc = p.nc;
@@ -843,7 +846,7 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
     __syncthreads();
     const int max_phases = (nr < nc ? nr : nc) + 2;
     int phases = 0, card = 0, status = 0;
-    long long levels_total = 0, eps_total = 0;
+    long long levels_total = 0, eps_total = 0, ins_total = 0;
     int free_total = 0, iso_free = 0;
     block_full_init<WR, NC>(p, sm, cnt, free_total, iso_free);
     int n_roots = sm.qn;
@@ -873,6 +876,7 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
             const int tail = sm.qn;
             const int eps = sm.qbase;
             ++levels;
+            ins_total += tail - qe;
             if (tail == qe) { n_ep = eps; break; }  // no vertex inserted
             if (p.mode == 1 && eps > 0) { n_ep = eps; break; }  // APsB
             if (levels > nc + 2) { status = -4; n_ep = eps; break; }
@@ -948,9 +952,10 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
         }
     }
     card_out = card;
-    phases_out = phases + 1;
+    phases_out = phases + (n_roots == 0 ? 1 : 0);  // no root left: Algorithm 1's last search finds nothing
     levels_out = levels_total;
     eps_out = eps_total;
+    ins_out = ins_total;
     __syncthreads();
     return status;
 }

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(1024, 1) k_serve(ServeParams sp) {
         p.mode = sp.mode;
         p.one_ep = sp.one_ep;
         int card = 0, phases = 0, status = 0;
-        long long levels = 0, eps = 0;
+        long long levels = 0, eps = 0, ins = 0;
         // the CSR came from the host: check it before any indexed read
         if (!bmd::block_check_csr<false>(p.nr, p.nc, s_d.nnz, p.col_ptr, p.row_idx, sm)) {
             status = BM_ERR_INVALID_CSR;
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(1024, 1) k_serve(ServeParams sp) {
             for (int r = threadIdx.x; r < p.nr; r += blockDim.x) __stcg(&p.rmatch[r], -1);
             for (int c = threadIdx.x; c < p.nc; c += blockDim.x) __stcg(&p.cmatch[c], -1);
             __syncthreads();
-            status = bmd::block_match_graph<WR, false>(p, s_d.greedy, sm, cnt, card, phases, levels, eps);
+            status = bmd::block_match_graph<WR, false>(p, s_d.greedy, sm, cnt, card, phases, levels, eps, ins);
         }
         if (threadIdx.x == 0) {
             SlotDone* d = &sp.done[t % sp.ring];

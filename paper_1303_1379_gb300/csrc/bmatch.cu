@@ -39,7 +39,7 @@ constexpr int kProfileCap = 4096;
 // nothing else).
 struct LeaderStats {
     unsigned long long t_start;
-    long long levels_total, levels_max, eps_total, ins_total;
+    long long levels_total, levels_max, eps_total, ins_total, roots_total;
     int levels, first_ep, last_ep;
 };
 
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
     int bid = 0;  // grid barriers passed
     const unsigned long long deadline = globaltimer() + (unsigned long long)p.total_ns;
     const bool leader = (blockIdx.x == 0 && threadIdx.x == 0);
-    if (leader) ls = LeaderStats{globaltimer(), 0, 0, 0, 0, 0, 0, 0};
+    if (leader) ls = LeaderStats{globaltimer(), 0, 0, 0, 0, 0, 0, 0, 0};
     // one-endpoint GPUBFS-WR: no FixMatching passes, roots carried to the next phase
     const bool incr = WR && p.one_ep && p.queue2 != nullptr && !p.bfs_only;
     int2* qcur = p.queue;
@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
     int status = 0;
     int n_roots = 0;
     int iso_free = 0;
+    int no_roots = 0;  // the loop ended because no column was left to search from
     if (ld_volatile(&ctl->err) != 0) goto out;  // input validation failed before launch
     {
         // ---- InitBfsArray (+ column half of FixMatching)
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
         if (leader) ctl->initial_card = card;
     }
     for (;;) {
-        if (n_roots == 0) break;  // no column left to search from
+        if (n_roots == 0) { no_roots = 1; break; }  // no column left to search from
         if (phases >= p.max_phases) {
             status = p.phase_limit_is_error ? -4 /*BM_ERR_ITER_LIMIT*/ : 1 /*BM_INCOMPLETE*/;
             break;
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
 
         // ---- BFS, level by level (Algorithm 1 inner loop)
         int qb = 0, qe = n_roots, lvl = L0, tail = n_roots;
-        if (leader) { ls.levels = 0; ls.first_ep = 0; ls.last_ep = 0; }
+        if (leader) { ls.levels = 0; ls.first_ep = 0; ls.last_ep = 0; ls.roots_total += n_roots; }
         for (;;) {
             const int s2 = step++;
             if (leader) { ctl->qcnt[(s2 + 1) % 3] = 0; ctl->ecnt[(s2 + 1) % 3] = 0; ctl->icnt[(s2 + 1) % 3] = 0; ctl->tcnt[(s2 + 1) % 3] = 0; }
@@ -183,11 +184,15 @@ out:
         int err = ld_volatile(&ctl->err);
         ctl->status = err != 0 ? err : status;
         ctl->card = card;
-        ctl->phases = phases + 1;  // counting the final search that found nothing
+        // Algorithm 1's outer iterations: every search, plus the final empty one
+        // that Algorithm 1 would run when no column is left to search from
+        ctl->phases = phases + no_roots;
+        ctl->searches = phases;
         ctl->levels = ls.levels_total;
         ctl->max_levels = ls.levels_max;
         ctl->endpoints = ls.eps_total;
         ctl->inserted = ls.ins_total;
+        ctl->roots = ls.roots_total;
         ctl->kernel_ns = (long long)(globaltimer() - ls.t_start);
     }
 }
@@ -445,8 +450,8 @@ int32_t run_host_loop(bm_ctx* ctx, const Params& p) {
     const int gb = grid_for(ctx, ctx->nc > ctx->nr ? ctx->nc : ctx->nr);
     const int blk = ctx->block;
     cudaStream_t st = ctx->stream;
-    int phases = 0, card = 0, status = 0;
-    long long levels_total = 0, levels_max = 0, eps_total = 0, ins_total = 0;
+    int phases = 0, card = 0, status = 0, no_roots = 0;
+    long long levels_total = 0, levels_max = 0, eps_total = 0, ins_total = 0, roots_total = 0;
     int step = 0;
     auto clear_slot = [&](int slot) -> int32_t {
         BM_CUDA(ctx, cudaMemsetAsync(&ctx->ctl->qcnt[slot], 0, sizeof(int32_t), st));
@@ -473,9 +478,10 @@ int32_t run_host_loop(bm_ctx* ctx, const Params& p) {
         if (phases == 0) {
             BM_CUDA(ctx, cudaMemcpyAsync(&ctx->ctl->initial_card, &card, sizeof(int), cudaMemcpyHostToDevice, st));
         }
-        if (n_roots == 0) break;
+        if (n_roots == 0) { no_roots = 1; break; }
         if (phases >= p.max_phases) { status = p.phase_limit_is_error ? BM_ERR_ITER_LIMIT : BM_INCOMPLETE; break; }
         ++phases;
+        roots_total += n_roots;
         int qb = 0, qe = n_roots, lvl = L0, n_ep = 0, levels = 0, first_ep = 0, last_ep = 0;
         for (;;) {
             int s2 = step++;
@@ -524,7 +530,9 @@ int32_t run_host_loop(bm_ctx* ctx, const Params& p) {
     Ctl fin = *h;
     fin.status = fin.err ? fin.err : status;
     fin.card = card;
-    fin.phases = phases + 1;
+    fin.phases = phases + no_roots;
+    fin.searches = phases;
+    fin.roots = roots_total;
     fin.levels = levels_total;
     fin.max_levels = levels_max;
     fin.endpoints = eps_total;
@@ -583,6 +591,11 @@ int32_t finish(bm_ctx* ctx, int32_t* card_out, bm_stats* stats) {
         stats->edges_to_matched = h.edges_matched;
         stats->alternate_steps = h.alt_steps;
         stats->kernel_ns = h.kernel_ns;
+        stats->roots = h.roots;
+        if (ctx->opt.driver == BM_DRIVER_PERSISTENT) {
+            stats->grid = ctx->coop_grid[ctx->opt.bfs == BM_GPUBFS_WR ? 1 : 0];
+            stats->block = ctx->block;
+        }
     }
     return status;
 }
@@ -899,8 +912,7 @@ int32_t bm_phase_profile(bm_ctx* ctx, int32_t cap, int32_t* levels, int32_t* end
     if (ctx->sticky) return BM_ERR_STATE;
     int32_t rc = sync_ctl(ctx);
     if (rc) return rc;
-    int n = ctx->h_ctl->phases - 1;  // phases that searched with at least one root
-    if (n < 0) n = 0;
+    int n = ctx->h_ctl->searches;  // phases that searched with at least one root
     if (n > kProfileCap) n = kProfileCap;
     if (n > cap) n = cap;
     *n_out = n;

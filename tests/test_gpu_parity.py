@@ -110,6 +110,46 @@ def test_gpubfs_levels_equal_alternating_bfs(gname):
         assert row in g.row_idx[g.col_ptr[c_prev]:g.col_ptr[c_prev + 1]]
 
 
+def level_widths(level):
+    """Columns per BFS level (the frontier each level expands), level L0 = 2 first."""
+    vals, counts = np.unique(level[level >= 2], return_counts=True)
+    return dict(zip(vals.tolist(), counts.tolist()))
+
+
+@pytest.mark.parametrize("gname", ["uniform1M", "rmat21"])
+@pytest.mark.parametrize("driver", [0, 1], ids=["persistent", "host"])
+def test_gpubfs_levels_equal_alternating_bfs_wide(gname, driver):
+    """The exact level pin on frontiers far wider than the grid: the
+    persistent kernel expands a level of at most 32,768 columns through the
+    row stamps, a level of up to one tile per block (grid x 512 columns) by
+    block index with a level CAS, and a wider level in guided ranges from a
+    position counter; the host loop's per-level launches take fixed tiles from
+    a counter.  Every path must give each column its alternating BFS distance
+    and claim exactly the reachable free rows (Algorithm 2, APFB)."""
+    g = {"uniform1M": lambda: synth.uniform_graph(1_000_000, 1_000_000, 4, seed=4),
+         "rmat21": lambda: synth.workload("rmat21")}[gname]()
+    rm0, cm0, _ = oracle.greedy(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+    want_level, want_reached = oracle.bfs_levels(g.n_rows, g.n_cols, g.col_ptr, g.row_idx, rm0, cm0, L0=2)
+    # the frontier of level L0 is the free columns that have rows
+    widths = level_widths(want_level)
+    widths[2] = int(((cm0 < 0) & (np.diff(g.col_ptr) > 0)).sum())
+    level, root, pred, ends = bfs_gpu(g, (rm0, cm0), mode=0, bfs=0, driver=driver)
+    assert np.array_equal(level, want_level)
+    assert np.array_equal(np.sort(ends), np.flatnonzero(want_reached))
+    assert np.all(root == -1)
+    reached = np.flatnonzero(level > 2)
+    assert np.all(level[pred[cm0[reached]]] == level[reached] - 1)
+    if driver == 0:
+        # the three claim paths were all taken (widths from the oracle)
+        stats = gpu_match(g, (rm0, cm0), mode=0, bfs=0)[3]
+        one_tile_per_block = stats["grid"] * stats["block"]
+        w = list(widths.values())
+        assert any(x > one_tile_per_block for x in w), (widths, one_tile_per_block)
+        assert any(x <= 32768 for x in w)
+        if gname == "uniform1M":
+            assert any(32768 < x <= one_tile_per_block for x in w), (widths, one_tile_per_block)
+
+
 @pytest.mark.parametrize("one_ep", [1, 0])
 def test_gpubfs_wr_trees_are_valid(one_ep):
     """GPUBFS-WR trees depend on timing; check what must hold: levels never
@@ -333,7 +373,7 @@ def test_phase_profile_matches_counters(c1, driver):
         res = m.match()
         levels, ends, first, last = m.phase_profile()
     st = res.stats
-    assert len(levels) == st["phases"] - 1
+    assert len(levels) == st["phases"]  # every outer iteration searched; the last found nothing
     assert int(levels.sum()) == st["levels"] and int(levels.max()) == st["max_levels_in_phase"]
     assert int(ends.sum()) == st["endpoints"]
     assert np.all((ends > 0) == (first > 0))
