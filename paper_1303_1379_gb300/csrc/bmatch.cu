@@ -269,18 +269,44 @@ __global__ void k_fill(int32_t* a, long long n, int v) {
 }
 
 // Cheap matching: each unmatched column claims the first unmatched row of its
-// list by CAS.  A column stays unmatched only if all its rows were taken, so
-// the result is maximal.  The scan looks at 4 rows per step with their loads
-// in flight together (hub columns can pass many taken rows).
-__global__ void k_greedy(int nc, const int32_t* __restrict__ cp, const int32_t* __restrict__ ri,
-                         int32_t* rm, int32_t* cm, const Ctl* ctl = nullptr) {
+// list by CAS.  A column stays unmatched only if all its rows were taken (a
+// claim is never given back), so the result is maximal.  Three launches take
+// the columns by degree, shortest lists first (a column with few rows has few
+// chances, so it chooses before the hubs, which can still find rows far down
+// their lists):
+//  * light columns (at most GREEDY_LIGHT rows): one thread each, 4 rows per
+//    step with the loads in flight together;
+//  * medium columns (up to GREEDY_MEDIUM rows): one warp each, 32 x GREEDY_U
+//    rows per step;
+//  * heavy columns (R-MAT hubs reach 60,000 rows, most of them taken by then):
+//    one block each, blockDim x GREEDY_U rows per step.
+// In the cooperative scans every thread loads GREEDY_U rows and their
+// matches, the free ones are marked, and their holders try the CAS in list
+// order until one wins, so a column still takes the first row of its list
+// that was free when it looked.
+constexpr int GREEDY_LIGHT = 32;
+constexpr int GREEDY_MEDIUM = 2048;
+constexpr int GREEDY_U = 4;
+
+__device__ __forceinline__ void greedy_col_range(int c, int nc, const int32_t* __restrict__ cp, const int32_t* cm,
+                                                 int& beg, int& end) {
+    beg = end = 0;
+    if (c < nc && cm[c] == -1) {
+        beg = __ldg(&cp[c]);
+        end = __ldg(&cp[c + 1]);
+    }
+}
+
+__global__ void k_greedy_light(int nc, const int32_t* __restrict__ cp, const int32_t* __restrict__ ri,
+                               int32_t* rm, int32_t* cm, const Ctl* ctl) {
     // after an asynchronous CSR check on the same stream: an invalid CSR is not read
     if (ctl && bmd::ld_volatile(&ctl->err) != 0) return;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
-        if (cm[c] != -1) continue;
-        const int end = __ldg(&cp[c + 1]);
+        int beg, end;
+        greedy_col_range(c, nc, cp, cm, beg, end);
+        if (end - beg > GREEDY_LIGHT) continue;
         bool done = false;
-        for (int e = __ldg(&cp[c]); e < end && !done; e += 4) {
+        for (int e = beg; e < end && !done; e += 4) {
             int r[4], m[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) r[u] = e + u < end ? __ldg(&ri[e + u]) : -1;
@@ -295,6 +321,134 @@ __global__ void k_greedy(int nc, const int32_t* __restrict__ cp, const int32_t* 
             }
         }
     }
+}
+
+__global__ void k_greedy_medium(int nc, const int32_t* __restrict__ cp, const int32_t* __restrict__ ri,
+                                int32_t* rm, int32_t* cm, const Ctl* ctl) {
+    if (ctl && bmd::ld_volatile(&ctl->err) != 0) return;
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long base = warp * 32; base < nc; base += nwarps * 32) {  // warp-uniform
+        const int c = (int)(base + lane);
+        int beg, end;
+        greedy_col_range(c, nc, cp, cm, beg, end);
+        unsigned todo = __ballot_sync(bmd::FULL, end - beg > GREEDY_LIGHT && end - beg <= GREEDY_MEDIUM);
+        while (todo) {  // warp-uniform
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int hc = __shfl_sync(bmd::FULL, c, src);
+            const int hb = __shfl_sync(bmd::FULL, beg, src);
+            const int he = __shfl_sync(bmd::FULL, end, src);
+            bool done = false;
+            for (int e0 = hb; e0 < he && !done; e0 += 32 * GREEDY_U) {  // warp-uniform
+                int r[GREEDY_U], m[GREEDY_U];
+#pragma unroll
+                for (int u = 0; u < GREEDY_U; ++u) {
+                    const int e = e0 + u * 32 + lane;
+                    r[u] = e < he ? __ldg(&ri[e]) : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < GREEDY_U; ++u) m[u] = r[u] >= 0 ? bmd::ld_volatile(&rm[r[u]]) : 0;
+#pragma unroll
+                for (int u = 0; u < GREEDY_U; ++u) {
+                    unsigned free_lanes = __ballot_sync(bmd::FULL, m[u] == -1);
+                    while (free_lanes && !done) {  // warp-uniform: lowest list position first
+                        const int l = __ffs(free_lanes) - 1;
+                        free_lanes &= free_lanes - 1;
+                        int won = 0;
+                        if (lane == l) won = atomicCAS(&rm[r[u]], -1, hc) == -1;
+                        won = __shfl_sync(bmd::FULL, won, l);
+                        if (won) {
+                            if (lane == l) cm[hc] = r[u];
+                            done = true;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_greedy_heavy(int nc, const int32_t* __restrict__ cp,
+                                                       const int32_t* __restrict__ ri, int32_t* rm, int32_t* cm,
+                                                       const Ctl* ctl) {
+    if (ctl && bmd::ld_volatile(&ctl->err) != 0) return;
+    __shared__ int s_cols[1024];
+    __shared__ int s_n, s_pos, s_done;
+    const int T = blockDim.x, t = threadIdx.x;
+    for (long long base = (long long)blockIdx.x * T; base < nc; base += (long long)gridDim.x * T) {  // block-uniform
+        if (t == 0) s_n = 0;
+        __syncthreads();
+        {
+            const int c = (int)(base + t);
+            int beg, end;
+            greedy_col_range(c, nc, cp, cm, beg, end);
+            if (end - beg > GREEDY_MEDIUM) s_cols[atomicAdd(&s_n, 1)] = c;
+        }
+        __syncthreads();
+        const int n = s_n;
+        for (int k = 0; k < n; ++k) {  // block-uniform
+            const int hc = s_cols[k];
+            const int hb = __ldg(&cp[hc]), he = __ldg(&cp[hc + 1]);
+            if (t == 0) s_done = 0;
+            __syncthreads();
+            for (int e0 = hb; e0 < he; e0 += T * GREEDY_U) {  // block-uniform
+                int r[GREEDY_U], m[GREEDY_U];
+#pragma unroll
+                for (int u = 0; u < GREEDY_U; ++u) {
+                    const int e = e0 + u * T + t;
+                    r[u] = e < he ? __ldg(&ri[e]) : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < GREEDY_U; ++u) m[u] = r[u] >= 0 ? bmd::ld_volatile(&rm[r[u]]) : 0;
+                // the first free row of the window in list order: smallest (u, t) with a free row
+                int pos = 0x7fffffff;
+#pragma unroll
+                for (int u = GREEDY_U - 1; u >= 0; --u)
+                    if (m[u] == -1) pos = u * T + t;
+                if (t == 0) s_pos = 0x7fffffff;
+                __syncthreads();
+                if (pos != 0x7fffffff) atomicMin(&s_pos, pos);
+                __syncthreads();
+                // candidates in list order; a failed CAS (taken meanwhile) moves to the next free one
+                while (s_pos != 0x7fffffff && !s_done) {  // block-uniform
+                    const int mypos = s_pos;
+                    __syncthreads();
+                    if (t == mypos % T) {
+                        const int u = mypos / T;
+                        int rr = -1;
+#pragma unroll
+                        for (int v = 0; v < GREEDY_U; ++v) if (v == u) rr = r[v];
+                        if (atomicCAS(&rm[rr], -1, hc) == -1) {
+                            cm[hc] = rr;
+                            s_done = 1;
+                        }
+                        s_pos = 0x7fffffff;
+                    }
+                    __syncthreads();
+                    if (!s_done) {
+                        int next = 0x7fffffff;
+#pragma unroll
+                        for (int u = GREEDY_U - 1; u >= 0; --u)
+                            if (m[u] == -1 && u * T + t > mypos) next = u * T + t;
+                        if (next != 0x7fffffff) atomicMin(&s_pos, next);
+                    }
+                    __syncthreads();
+                }
+                if (s_done) break;
+            }
+            __syncthreads();  // s_done is reset for the next column
+        }
+    }
+}
+
+// The cheap matching (Section 4) on the device: light, medium and heavy columns in this order.
+void launch_greedy(int nc, const int32_t* cp, const int32_t* ri, int32_t* rm, int32_t* cm, const Ctl* ctl,
+                   int grid, int block, cudaStream_t st) {
+    k_greedy_light<<<grid, block, 0, st>>>(nc, cp, ri, rm, cm, ctl);
+    k_greedy_medium<<<grid, block, 0, st>>>(nc, cp, ri, rm, cm, ctl);
+    k_greedy_heavy<<<grid, block, 0, st>>>(nc, cp, ri, rm, cm, ctl);
 }
 
 __global__ void k_count_matched(int nc, const int32_t* __restrict__ cm, Ctl* ctl) {
@@ -776,7 +930,8 @@ int32_t bm_greedy(bm_ctx* ctx, int32_t* card_out) {
     cudaStream_t st = ctx->stream;
     BM_CUDA(ctx, cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), st));
     if (ctx->nc) {
-        k_greedy<<<grid_for(ctx, ctx->nc), ctx->block, 0, st>>>(ctx->nc, ctx->col_ptr, ctx->row_idx, ctx->rmatch, ctx->cmatch);
+        launch_greedy(ctx->nc, ctx->col_ptr, ctx->row_idx, ctx->rmatch, ctx->cmatch, nullptr, grid_for(ctx, ctx->nc),
+                      ctx->block, st);
         BM_CUDA(ctx, cudaGetLastError());
         k_count_matched<<<grid_for(ctx, ctx->nc), ctx->block, 0, st>>>(ctx->nc, ctx->cmatch, ctx->ctl);
         BM_CUDA(ctx, cudaGetLastError());
@@ -1141,7 +1296,7 @@ int32_t bmi::enqueue_match(bmd::Params p, long long nnz, bool wr, int greedy, cu
         (void)cudaGetLastError();
         return BM_ERR_CUDA;
     }
-    if (greedy) k_greedy<<<grid_of(p.nc), B, 0, st>>>(p.nc, p.col_ptr, p.row_idx, p.rmatch, p.cmatch, p.ctl);
+    if (greedy) launch_greedy(p.nc, p.col_ptr, p.row_idx, p.rmatch, p.cmatch, p.ctl, grid_of(p.nc), B, st);
     if (cudaGetLastError() != cudaSuccess) return BM_ERR_CUDA;
     p.bfs_only = 0;
     p.profile = nullptr;
