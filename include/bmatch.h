@@ -157,7 +157,8 @@ BM_API int32_t bm_set_options(bm_ctx *ctx, const bm_options *opt);
  * Section 4): every unmatched column scans its rows in order and claims the
  * first unmatched one with an atomic compare-and-swap.  Columns are taken in
  * three passes by degree, shortest lists first (at most 32 rows: a thread
- * each; up to 2048: a warp each; longer: a block each).  The result is a
+ * each; up to 2048: a warp each, longer: a block each, dealt from lists the
+ * first pass builds in the context's queue).  The result is a
  * maximal matching added to the installed one; which maximal matching it is
  * depends on thread timing.  *card_out (host, nullable) gets |M|. */
 BM_API int32_t bm_greedy(bm_ctx *ctx, int32_t *card_out);

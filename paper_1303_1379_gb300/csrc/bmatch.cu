@@ -275,7 +275,9 @@ __global__ void k_fill(int32_t* a, long long n, int v) {
 // chances, so it chooses before the hubs, which can still find rows far down
 // their lists):
 //  * light columns (at most GREEDY_LIGHT rows): one thread each, 4 rows per
-//    step with the loads in flight together;
+//    step with the loads in flight together; this pass also lists the medium
+//    and heavy columns (R-MAT puts its hubs at neighbouring ids, so the later
+//    passes deal them out from these lists instead of by id);
 //  * medium columns (up to GREEDY_MEDIUM rows): one warp each, 32 x GREEDY_U
 //    rows per step;
 //  * heavy columns (R-MAT hubs reach 60,000 rows, most of them taken by then):
@@ -288,23 +290,28 @@ constexpr int GREEDY_LIGHT = 32;
 constexpr int GREEDY_MEDIUM = 2048;
 constexpr int GREEDY_U = 4;
 
-__device__ __forceinline__ void greedy_col_range(int c, int nc, const int32_t* __restrict__ cp, const int32_t* cm,
-                                                 int& beg, int& end) {
-    beg = end = 0;
-    if (c < nc && cm[c] == -1) {
-        beg = __ldg(&cp[c]);
-        end = __ldg(&cp[c + 1]);
-    }
-}
+struct GreedyLists {
+    int32_t* medium;  // [nc] columns of the medium pass
+    int32_t* heavy;   // [nc] columns of the heavy pass
+    int32_t* count;   // [2] their lengths, zero before the light pass
+};
 
 __global__ void k_greedy_light(int nc, const int32_t* __restrict__ cp, const int32_t* __restrict__ ri,
-                               int32_t* rm, int32_t* cm, const Ctl* ctl) {
+                               int32_t* rm, int32_t* cm, GreedyLists gl, const Ctl* ctl) {
     // after an asynchronous CSR check on the same stream: an invalid CSR is not read
     if (ctl && bmd::ld_volatile(&ctl->err) != 0) return;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
-        int beg, end;
-        greedy_col_range(c, nc, cp, cm, beg, end);
-        if (end - beg > GREEDY_LIGHT) continue;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < nc; base += stride) {  // block-uniform
+        const int c = (int)(base + threadIdx.x);
+        int beg = 0, end = 0;
+        if (c < nc && cm[c] == -1) {
+            beg = __ldg(&cp[c]);
+            end = __ldg(&cp[c + 1]);
+        }
+        const int deg = end - beg;
+        if (deg > GREEDY_MEDIUM) bmd::push(gl.heavy, 0, &gl.count[1], c);
+        else if (deg > GREEDY_LIGHT) bmd::push(gl.medium, 0, &gl.count[0], c);
+        if (deg > GREEDY_LIGHT) continue;
         bool done = false;
         for (int e = beg; e < end && !done; e += 4) {
             int r[4], m[4];
@@ -323,46 +330,38 @@ __global__ void k_greedy_light(int nc, const int32_t* __restrict__ cp, const int
     }
 }
 
-__global__ void k_greedy_medium(int nc, const int32_t* __restrict__ cp, const int32_t* __restrict__ ri,
-                                int32_t* rm, int32_t* cm, const Ctl* ctl) {
+__global__ void k_greedy_medium(const int32_t* __restrict__ cp, const int32_t* __restrict__ ri, int32_t* rm,
+                                int32_t* cm, GreedyLists gl, const Ctl* ctl) {
     if (ctl && bmd::ld_volatile(&ctl->err) != 0) return;
     const int lane = threadIdx.x & 31;
+    const int n = gl.count[0];
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long base = warp * 32; base < nc; base += nwarps * 32) {  // warp-uniform
-        const int c = (int)(base + lane);
-        int beg, end;
-        greedy_col_range(c, nc, cp, cm, beg, end);
-        unsigned todo = __ballot_sync(bmd::FULL, end - beg > GREEDY_LIGHT && end - beg <= GREEDY_MEDIUM);
-        while (todo) {  // warp-uniform
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int hc = __shfl_sync(bmd::FULL, c, src);
-            const int hb = __shfl_sync(bmd::FULL, beg, src);
-            const int he = __shfl_sync(bmd::FULL, end, src);
-            bool done = false;
-            for (int e0 = hb; e0 < he && !done; e0 += 32 * GREEDY_U) {  // warp-uniform
-                int r[GREEDY_U], m[GREEDY_U];
+    for (long long k = warp; k < n; k += nwarps) {  // warp-uniform
+        const int hc = gl.medium[k];
+        const int hb = __ldg(&cp[hc]), he = __ldg(&cp[hc + 1]);
+        bool done = false;
+        for (int e0 = hb; e0 < he && !done; e0 += 32 * GREEDY_U) {  // warp-uniform
+            int r[GREEDY_U], m[GREEDY_U];
 #pragma unroll
-                for (int u = 0; u < GREEDY_U; ++u) {
-                    const int e = e0 + u * 32 + lane;
-                    r[u] = e < he ? __ldg(&ri[e]) : -1;
-                }
+            for (int u = 0; u < GREEDY_U; ++u) {
+                const int e = e0 + u * 32 + lane;
+                r[u] = e < he ? __ldg(&ri[e]) : -1;
+            }
 #pragma unroll
-                for (int u = 0; u < GREEDY_U; ++u) m[u] = r[u] >= 0 ? bmd::ld_volatile(&rm[r[u]]) : 0;
+            for (int u = 0; u < GREEDY_U; ++u) m[u] = r[u] >= 0 ? bmd::ld_volatile(&rm[r[u]]) : 0;
 #pragma unroll
-                for (int u = 0; u < GREEDY_U; ++u) {
-                    unsigned free_lanes = __ballot_sync(bmd::FULL, m[u] == -1);
-                    while (free_lanes && !done) {  // warp-uniform: lowest list position first
-                        const int l = __ffs(free_lanes) - 1;
-                        free_lanes &= free_lanes - 1;
-                        int won = 0;
-                        if (lane == l) won = atomicCAS(&rm[r[u]], -1, hc) == -1;
-                        won = __shfl_sync(bmd::FULL, won, l);
-                        if (won) {
-                            if (lane == l) cm[hc] = r[u];
-                            done = true;
-                        }
+            for (int u = 0; u < GREEDY_U; ++u) {
+                unsigned free_lanes = __ballot_sync(bmd::FULL, m[u] == -1);
+                while (free_lanes && !done) {  // warp-uniform: lowest list position first
+                    const int l = __ffs(free_lanes) - 1;
+                    free_lanes &= free_lanes - 1;
+                    int won = 0;
+                    if (lane == l) won = atomicCAS(&rm[r[u]], -1, hc) == -1;
+                    won = __shfl_sync(bmd::FULL, won, l);
+                    if (won) {
+                        if (lane == l) cm[hc] = r[u];
+                        done = true;
                     }
                 }
             }
@@ -370,85 +369,76 @@ __global__ void k_greedy_medium(int nc, const int32_t* __restrict__ cp, const in
     }
 }
 
-__global__ void __launch_bounds__(1024) k_greedy_heavy(int nc, const int32_t* __restrict__ cp,
-                                                       const int32_t* __restrict__ ri, int32_t* rm, int32_t* cm,
-                                                       const Ctl* ctl) {
+__global__ void __launch_bounds__(1024) k_greedy_heavy(const int32_t* __restrict__ cp, const int32_t* __restrict__ ri,
+                                                       int32_t* rm, int32_t* cm, GreedyLists gl, const Ctl* ctl) {
     if (ctl && bmd::ld_volatile(&ctl->err) != 0) return;
-    __shared__ int s_cols[1024];
-    __shared__ int s_n, s_pos, s_done;
+    __shared__ int s_pos, s_done;
     const int T = blockDim.x, t = threadIdx.x;
-    for (long long base = (long long)blockIdx.x * T; base < nc; base += (long long)gridDim.x * T) {  // block-uniform
-        if (t == 0) s_n = 0;
+    const int n = gl.count[1];
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {  // block-uniform
+        const int hc = gl.heavy[k];
+        const int hb = __ldg(&cp[hc]), he = __ldg(&cp[hc + 1]);
+        if (t == 0) s_done = 0;
         __syncthreads();
-        {
-            const int c = (int)(base + t);
-            int beg, end;
-            greedy_col_range(c, nc, cp, cm, beg, end);
-            if (end - beg > GREEDY_MEDIUM) s_cols[atomicAdd(&s_n, 1)] = c;
-        }
-        __syncthreads();
-        const int n = s_n;
-        for (int k = 0; k < n; ++k) {  // block-uniform
-            const int hc = s_cols[k];
-            const int hb = __ldg(&cp[hc]), he = __ldg(&cp[hc + 1]);
-            if (t == 0) s_done = 0;
-            __syncthreads();
-            for (int e0 = hb; e0 < he; e0 += T * GREEDY_U) {  // block-uniform
-                int r[GREEDY_U], m[GREEDY_U];
+        for (int e0 = hb; e0 < he; e0 += T * GREEDY_U) {  // block-uniform
+            int r[GREEDY_U], m[GREEDY_U];
 #pragma unroll
-                for (int u = 0; u < GREEDY_U; ++u) {
-                    const int e = e0 + u * T + t;
-                    r[u] = e < he ? __ldg(&ri[e]) : -1;
-                }
-#pragma unroll
-                for (int u = 0; u < GREEDY_U; ++u) m[u] = r[u] >= 0 ? bmd::ld_volatile(&rm[r[u]]) : 0;
-                // the first free row of the window in list order: smallest (u, t) with a free row
-                int pos = 0x7fffffff;
-#pragma unroll
-                for (int u = GREEDY_U - 1; u >= 0; --u)
-                    if (m[u] == -1) pos = u * T + t;
-                if (t == 0) s_pos = 0x7fffffff;
-                __syncthreads();
-                if (pos != 0x7fffffff) atomicMin(&s_pos, pos);
-                __syncthreads();
-                // candidates in list order; a failed CAS (taken meanwhile) moves to the next free one
-                while (s_pos != 0x7fffffff && !s_done) {  // block-uniform
-                    const int mypos = s_pos;
-                    __syncthreads();
-                    if (t == mypos % T) {
-                        const int u = mypos / T;
-                        int rr = -1;
-#pragma unroll
-                        for (int v = 0; v < GREEDY_U; ++v) if (v == u) rr = r[v];
-                        if (atomicCAS(&rm[rr], -1, hc) == -1) {
-                            cm[hc] = rr;
-                            s_done = 1;
-                        }
-                        s_pos = 0x7fffffff;
-                    }
-                    __syncthreads();
-                    if (!s_done) {
-                        int next = 0x7fffffff;
-#pragma unroll
-                        for (int u = GREEDY_U - 1; u >= 0; --u)
-                            if (m[u] == -1 && u * T + t > mypos) next = u * T + t;
-                        if (next != 0x7fffffff) atomicMin(&s_pos, next);
-                    }
-                    __syncthreads();
-                }
-                if (s_done) break;
+            for (int u = 0; u < GREEDY_U; ++u) {
+                const int e = e0 + u * T + t;
+                r[u] = e < he ? __ldg(&ri[e]) : -1;
             }
-            __syncthreads();  // s_done is reset for the next column
+#pragma unroll
+            for (int u = 0; u < GREEDY_U; ++u) m[u] = r[u] >= 0 ? bmd::ld_volatile(&rm[r[u]]) : 0;
+            // window position of this thread's first free row (list order: u major, thread minor)
+            int pos = 0x7fffffff;
+#pragma unroll
+            for (int u = GREEDY_U - 1; u >= 0; --u)
+                if (m[u] == -1) pos = u * T + t;
+            if (t == 0) s_pos = 0x7fffffff;
+            __syncthreads();
+            if (pos != 0x7fffffff) atomicMin(&s_pos, pos);
+            __syncthreads();
+            // candidates in list order; a failed CAS (taken meanwhile) moves on to the next free one
+            while (s_pos != 0x7fffffff && !s_done) {  // block-uniform
+                const int mypos = s_pos;
+                __syncthreads();  // every thread has read s_pos
+                if (t == mypos % T) {
+                    const int u = mypos / T;
+                    int rr = -1;
+#pragma unroll
+                    for (int v = 0; v < GREEDY_U; ++v)
+                        if (v == u) rr = r[v];
+                    if (atomicCAS(&rm[rr], -1, hc) == -1) {
+                        cm[hc] = rr;
+                        s_done = 1;
+                    }
+                    s_pos = 0x7fffffff;
+                }
+                __syncthreads();
+                if (!s_done) {
+                    int next = 0x7fffffff;
+#pragma unroll
+                    for (int u = GREEDY_U - 1; u >= 0; --u)
+                        if (m[u] == -1 && u * T + t > mypos) next = u * T + t;
+                    if (next != 0x7fffffff) atomicMin(&s_pos, next);
+                }
+                __syncthreads();
+            }
+            if (s_done) break;
         }
+        __syncthreads();  // s_done is reset for the next column
     }
 }
 
-// The cheap matching (Section 4) on the device: light, medium and heavy columns in this order.
+// The cheap matching (Section 4) on the device: light, medium and heavy
+// columns in this order.  `lists` is scratch of 2 x nc int32 (the context's
+// queue, free before a match) and `count` two int32 cleared beforehand.
 void launch_greedy(int nc, const int32_t* cp, const int32_t* ri, int32_t* rm, int32_t* cm, const Ctl* ctl,
-                   int grid, int block, cudaStream_t st) {
-    k_greedy_light<<<grid, block, 0, st>>>(nc, cp, ri, rm, cm, ctl);
-    k_greedy_medium<<<grid, block, 0, st>>>(nc, cp, ri, rm, cm, ctl);
-    k_greedy_heavy<<<grid, block, 0, st>>>(nc, cp, ri, rm, cm, ctl);
+                   int32_t* lists, int32_t* count, int grid, int block, cudaStream_t st) {
+    const GreedyLists gl{lists, lists + nc, count};
+    k_greedy_light<<<grid, block, 0, st>>>(nc, cp, ri, rm, cm, gl, ctl);
+    k_greedy_medium<<<grid, block, 0, st>>>(cp, ri, rm, cm, gl, ctl);
+    k_greedy_heavy<<<grid, block, 0, st>>>(cp, ri, rm, cm, gl, ctl);
 }
 
 __global__ void k_count_matched(int nc, const int32_t* __restrict__ cm, Ctl* ctl) {
@@ -930,8 +920,8 @@ int32_t bm_greedy(bm_ctx* ctx, int32_t* card_out) {
     cudaStream_t st = ctx->stream;
     BM_CUDA(ctx, cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), st));
     if (ctx->nc) {
-        launch_greedy(ctx->nc, ctx->col_ptr, ctx->row_idx, ctx->rmatch, ctx->cmatch, nullptr, grid_for(ctx, ctx->nc),
-                      ctx->block, st);
+        launch_greedy(ctx->nc, ctx->col_ptr, ctx->row_idx, ctx->rmatch, ctx->cmatch, nullptr, (int32_t*)ctx->queue,
+                      &ctx->ctl->qcnt[0], grid_for(ctx, ctx->nc), ctx->block, st);
         BM_CUDA(ctx, cudaGetLastError());
         k_count_matched<<<grid_for(ctx, ctx->nc), ctx->block, 0, st>>>(ctx->nc, ctx->cmatch, ctx->ctl);
         BM_CUDA(ctx, cudaGetLastError());
@@ -1296,7 +1286,16 @@ int32_t bmi::enqueue_match(bmd::Params p, long long nnz, bool wr, int greedy, cu
         (void)cudaGetLastError();
         return BM_ERR_CUDA;
     }
-    if (greedy) launch_greedy(p.nc, p.col_ptr, p.row_idx, p.rmatch, p.cmatch, p.ctl, grid_of(p.nc), B, st);
+    if (greedy) {
+        // the cheap matching counts its lists in the control block's first two queue
+        // counters, which the matching kernel needs at zero
+        launch_greedy(p.nc, p.col_ptr, p.row_idx, p.rmatch, p.cmatch, p.ctl, (int32_t*)p.queue, &p.ctl->qcnt[0],
+                      grid_of(p.nc), B, st);
+        if (cudaMemsetAsync(&p.ctl->qcnt[0], 0, 2 * sizeof(int32_t), st) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return BM_ERR_CUDA;
+        }
+    }
     if (cudaGetLastError() != cudaSuccess) return BM_ERR_CUDA;
     p.bfs_only = 0;
     p.profile = nullptr;
