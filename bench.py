@@ -480,7 +480,13 @@ def serve_request_pool(n_distinct, seed=4):
 
 
 def bench_serving(args, torch, bmatch):
+    """The served stream.  With N ranks the stream is dealt by whole request
+    (each arriving request to the rank with the fewest edges so far, a deal
+    every rank computes alike) and each rank's own server matches its share;
+    results and timings meet after each run, off the data path."""
     import numpy as np
+    from paper_1303_1379_gb300 import shard
+    rank, world, _ = dist_env()
     t_gen = time.perf_counter()
     graphs = serve_request_pool(args.serve_distinct)
     t_gen = time.perf_counter() - t_gen
@@ -488,6 +494,7 @@ def bench_serving(args, torch, bmatch):
              torch.from_numpy(g.row_idx).pin_memory(), g.nnz) for g in graphs]
     N = args.serve_requests
     mean_edges = float(np.mean([h[4] for h in host]))
+    deal = shard.assign_stream([host[i % len(host)][4] for i in range(N)], world)
     sopts = {} if args.serve_exclusive_min_edges is None else {"exclusive_min_edges": args.serve_exclusive_min_edges}
     srv = bmatch.Server(pool_bytes=32 << 30, **sopts)
 
@@ -495,27 +502,33 @@ def bench_serving(args, torch, bmatch):
         """rate None: all N submitted at once (closed loop saturation)."""
         rng = np.random.default_rng(44)
         gaps = rng.exponential(1.0 / rate, N) if rate else np.zeros(N)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        sh = shard.StreamShard(srv, rank, deal)
         t0 = time.perf_counter()
         arrival = t0 + np.cumsum(gaps)
-        ids = []
         for i in range(N):
+            if not sh.mine(i):
+                continue
             if rate:
                 while time.perf_counter() < arrival[i]:
                     pass
             nr, nc, cp, ri, _ = host[i % len(host)]
-            ids.append(srv.submit(nr, nc, cp, ri))
-        lat, cards = [], []
-        for rid in ids:
-            info = srv.wait(rid, timeout_s=120)
-            if info["status"] != 0:
-                raise SystemExit(f"served request failed: {info}")
-            lat.append(info["latency_ns"] / 1e6)
-            cards.append(info["card"])
-            srv.release(rid)
-        span = time.perf_counter() - t0
+            sh.offer(i, nr, nc, cp, ri)
+        local = sh.drain(timeout_s=120)
+        span = shard.max_over_ranks([time.perf_counter() - t0],
+                                    device=torch.device("cuda", torch.cuda.current_device()))[0]
+        merged = shard.gather_results(local)
+        bad = [x for x in merged if x[1] != 0]
+        if bad or len(merged) != N:
+            raise SystemExit(f"served requests failed: {bad[:5]} ({len(merged)} of {N} returned)")
+        lat = [x[3] / 1e6 for x in merged]
+        cards = [x[2] for x in merged]
         return {"requests": N, "offered_rps": rate, "achieved_rps": N / span,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "edges_per_s": N * mean_edges / span, "span_s": span}, cards
+                "edges_per_s": N * mean_edges / span, "span_s": span,
+                "requests_per_rank": np.bincount(deal, minlength=world).tolist()}, cards
 
     sat, cards = run(None)
     lam = sat["achieved_rps"]
@@ -535,8 +548,8 @@ def bench_serving(args, torch, bmatch):
     # uploaded from the same pinned host arrays into a context, cheap
     # matching, Algorithm 1, |M| back, one request after another (contexts
     # made untimed, one per distinct graph)
-    ctxs = [bmatch.Matcher(nr, nc, nnz, None, None) for nr, nc, _, _, nnz in host]
-    n_one = min(N, args.serve_one_by_one)
+    ctxs = [bmatch.Matcher(nr, nc, nnz, None, None) for nr, nc, _, _, nnz in host] if world == 1 else []
+    n_one = min(N, args.serve_one_by_one) if world == 1 else 0
     same = True
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -551,15 +564,17 @@ def bench_serving(args, torch, bmatch):
     one_span = time.perf_counter() - t0
     for m in ctxs:
         m.close()
-    one = {"requests": n_one, "rps": n_one / one_span, "edges_per_s": n_one * mean_edges / one_span,
+    one = {"requests": n_one, "rps": n_one / one_span if n_one else None,
+           "edges_per_s": n_one * mean_edges / one_span if n_one else None,
            "same_cardinalities_as_served": bool(same),
-           "path": "bm_upload_csr + bm_greedy + bm_match per request, one after another"}
+           "path": "bm_upload_csr + bm_greedy + bm_match per request, one after another (one GPU)"}
     return {"workload": SERVE_WORKLOAD, "distinct_request_graphs": len(host),
             "requests_per_run": N, "mean_edges_per_request": mean_edges, "generate_s": round(t_gen, 1),
             "lambda_max_rps": lam, "runs": runs, "worker_grid": st["grid"], "worker_block": st["block"],
             "exclusive_min_edges": int(srv_opts_threshold), "requests_run_alone": int(st["exclusive_runs"]),
             "one_by_one": one, "one_by_one_rps": one["rps"],
-            "speedup_vs_one_by_one": lam / one["rps"],
+            "speedup_vs_one_by_one": lam / one["rps"] if one["rps"] else None,
+            "parallelism": f"stream dealt by request over {world} ranks" if world > 1 else "single GPU",
             "note": "request graphs recycled from the distinct set (host generation of every request "
                     "would dominate the run); each request is uploaded, matched and released on its own"}, \
         graphs, distinct
@@ -799,9 +814,9 @@ def run_ours(args):
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             batched["cpu_baseline"] = batched_cpu_baseline(bgraphs, bcards)
     served = None
-    if not args.no_serve and world == 1:
+    if not args.no_serve:
         served, sgraphs, scards = bench_serving(args, torch, bmatch)
-        if not args.no_cpu_baseline:
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
             import oracle
             t = time.perf_counter()
             ok = all(oracle.hopcroft_karp(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)[2] == scards[i]
