@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=4096,
                     help="graphs in the batched workload (smaller for profiling captures)")
+    ap.add_argument("--batch-geometry", default=None,
+                    help="threads x blocks per SM of the batched launch (e.g. 512x2) instead of the "
+                         "autotuner's choice (profiling captures)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-distinct", type=int, default=48)
@@ -353,7 +356,12 @@ def bench_batched(args, torch, bmatch, stream, flush):
     rm, cm = torch.empty_like(rm0), torch.empty_like(cm0)
     card = torch.zeros(G, dtype=torch.int32, device=dev)
     cands = [(256, 4), (256, 2), (512, 2), (512, 1), (1024, 1)]
-    best, tune_ms = bb.autotune(rm0, cm0, rm, cm, cands, greedy=True, reps=2)
+    if args.batch_geometry:
+        geo = tuple(int(x) for x in args.batch_geometry.split("x"))
+        bb.set_options(block_size=geo[0], blocks_per_sm=geo[1])
+        cands, best, tune_ms = [geo], 0, None
+    else:
+        best, tune_ms = bb.autotune(rm0, cm0, rm, cm, cands, greedy=True, reps=2)
     times = []
     for i in range(args.warmup + args.steps):
         rm.copy_(rm0)
