@@ -541,7 +541,7 @@ def bench_serving(args, torch, bmatch):
     sat, cards = run(None)
     lam = sat["achieved_rps"]
     runs = {"closed_loop": sat}
-    for frac in (0.5, 0.9):
+    for frac in (0.5, 0.75, 0.9):
         r, c2 = run(frac * lam)
         runs[f"poisson_{frac}"] = r
         if c2 != cards:

@@ -274,6 +274,65 @@ def test_gpu_greedy_is_maximal():
         assert np.all(rm[g.row_idx[g.col_ptr[c]:g.col_ptr[c + 1]]] >= 0)
 
 
+def heavy_mix_graph():
+    """Columns in all three passes of the cheap matching: 40 heavy columns of
+    2,500-6,000 rows over the first rows, 600 medium ones of 40-1,500 rows,
+    and 20,000 light ones of 1-8 rows, all competing for the same low rows
+    first (sorted lists), in shuffled column order."""
+    rng = np.random.default_rng(31)
+    nr = 30000
+    cols = []
+    for _ in range(40):
+        cols.append(np.sort(rng.choice(8000, int(rng.integers(2500, 6001)), replace=False)))
+    for _ in range(600):
+        cols.append(np.sort(rng.choice(12000, int(rng.integers(40, 1501)), replace=False)))
+    for _ in range(20000):
+        cols.append(np.sort(rng.choice(nr, int(rng.integers(1, 9)), replace=False)))
+    order = rng.permutation(len(cols))
+    cols = [cols[k] for k in order]
+    col_ptr = np.zeros(len(cols) + 1, np.int32)
+    col_ptr[1:] = np.cumsum([len(c) for c in cols])
+    return synth.Graph(nr, len(cols), col_ptr, np.concatenate(cols).astype(np.int32), "heavy-mix")
+
+
+def assert_maximal_extension(g, rm, cm, card, rm0=None, cm0=None):
+    assert oracle.validate(g.n_rows, g.n_cols, g.col_ptr, g.row_idx, rm, cm) == (0, card)
+    deg = np.diff(g.col_ptr)
+    free_cols = np.repeat(cm < 0, deg)  # per edge: is its column unmatched?
+    assert np.all(rm[g.row_idx[free_cols]] >= 0)  # maximal: no edge joins two free vertices
+    if rm0 is not None:  # the installed pairs stay
+        kept = cm0 >= 0
+        assert np.array_equal(cm[kept], cm0[kept]) and np.array_equal(rm[rm0 >= 0], rm0[rm0 >= 0])
+
+
+@pytest.mark.parametrize("gname", ["heavy-mix", "rmat18"])
+def test_gpu_greedy_passes_are_maximal(gname):
+    """The three passes of the cheap matching (a thread, a warp, a block per
+    column by degree) give a valid, maximal matching on graphs with columns
+    of every class, from the empty matching and on top of an installed one."""
+    g = heavy_mix_graph() if gname == "heavy-mix" else synth.rmat_graph(18, 1 << 22, seed=3)
+    deg = np.diff(g.col_ptr)
+    assert (deg > 2048).sum() >= 10 and ((deg > 32) & (deg <= 2048)).sum() >= 100 and (deg <= 32).sum() > 1000
+    cp, ri = to_dev(g)
+    rm = torch.empty(g.n_rows, dtype=torch.int32, device="cuda")
+    cm = torch.empty(g.n_cols, dtype=torch.int32, device="cuda")
+    with bmatch.Matcher(g.n_rows, g.n_cols, g.nnz, cp, ri) as m:
+        card = m.greedy()
+        m.get_matching(rm, cm)
+        assert_maximal_extension(g, rm.cpu().numpy(), cm.cpu().numpy(), card)
+        # on top of a partial matching: every third pair of the oracle's greedy start
+        rg, cg, _ = oracle.greedy(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+        rm0, cm0 = oracle.empty_matching(g.n_rows, g.n_cols)
+        for c in np.flatnonzero(cg >= 0)[::3]:
+            rm0[cg[c]], cm0[c] = c, cg[c]
+        m.set_matching(torch.from_numpy(rm0).cuda(), torch.from_numpy(cm0).cuda())
+        card = m.greedy()
+        m.get_matching(rm, cm)
+        assert_maximal_extension(g, rm.cpu().numpy(), cm.cpu().numpy(), card, rm0, cm0)
+        res = m.match()
+    assert res.card == oracle_max(g)
+
+
 def test_phase_limit_gives_valid_partial_matchings(c1):
     cards = []
     for k in (1, 2, 3):
