@@ -63,6 +63,8 @@ extern "C" {
 #define BM_ERR_UNSUPPORTED (-8)  /* device cannot run the cooperative launch   */
 #define BM_ERR_INVALID_MATCHING (-9) /* initial matching out of range or rmatch/cmatch not inverse */
 #define BM_ERR_TOO_LARGE (-10)   /* graph too large for bm_match_noalloc's fixed scratch */
+#define BM_ERR_CHECK (-11)       /* range-checked build (libbmatch_checked.so) only: an index
+                                    out of range, or rmatch/cmatch not inverse between phases */
 
 /* Algorithm 1: APFB keeps searching until no column is inserted; APsB stops
  * at the first level that reaches an unmatched row. */

@@ -27,6 +27,7 @@ BM_ERR_STATE = -7
 BM_ERR_UNSUPPORTED = -8
 BM_ERR_INVALID_MATCHING = -9
 BM_ERR_TOO_LARGE = -10
+BM_ERR_CHECK = -11
 
 BM_APFB, BM_APSB = 0, 1
 BM_GPUBFS, BM_GPUBFS_WR = 0, 1
@@ -125,17 +126,21 @@ I32P = ctypes.POINTER(ctypes.c_int32)
 
 
 def library_path() -> str:
-    return _build.LIB
+    """libbmatch.so, or its range-checked twin libbmatch_checked.so when the
+    environment sets BMATCH_CHECKED=1 (every index the kernels compute from
+    data is checked; a violation returns BM_ERR_CHECK).  Read once, at the
+    first load in the process."""
+    return _build.LIB_CHECKED if os.environ.get("BMATCH_CHECKED") == "1" else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Loads libbmatch.so (building it first if it is missing or stale)."""
+    """Loads the library (building it first if it is missing or stale)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
-            if build_if_missing and _build.is_stale():
-                _build.build()
+            path = library_path()
+            if build_if_missing and _build.is_stale(path):
+                _build.build(checked=path == _build.LIB_CHECKED)
             if not os.path.exists(path):
                 raise RuntimeError(f"CUDA library missing: {path} (run __graft_entry__.build())")
             lib = ctypes.CDLL(path)

@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(1024, 1) k_batch(BatchParams bp) {
         p.endpoints = bp.endpoints + ro;
         p.mode = bp.mode;
         p.one_ep = bp.one_ep;
+        p.chk = &bp.ctl->err;
         int card = 0, phases = 0;
         long long levels = 0, eps = 0, ins = 0;
         const int st = bmd::block_match_graph<WR, true, true>(p, bp.greedy, sm, cnt, card, phases, levels, eps, ins);

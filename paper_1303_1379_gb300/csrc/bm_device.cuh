@@ -115,6 +115,7 @@ struct Params {
     long long wait_ns;   // limit of one barrier wait
     long long total_ns;  // limit of the whole launch
     int32_t stamp_base;  // rvis stamp of phase k is stamp_base + k (k >= 1); above every stamp in rvis
+    int32_t* chk;        // range-checked build: error word set when an index is out of range (nullable)
 };
 
 // Per-block shared state of the steps.
@@ -155,6 +156,22 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 }
 
 __device__ __forceinline__ void set_error(Ctl* ctl, int code) { atomicCAS(&ctl->err, 0, code); }
+
+// Range-checked build (compiled with BM_CHECKED, the library libbmatch_checked.so):
+// every index the steps compute from data (a row id, a matched column, a root,
+// a queue entry) is checked before it is used; an index out of range records
+// BM_ERR_CHECK (-11) in p.chk and the access is skipped, so a fault in the
+// method's bookkeeping shows as a status instead of a stray memory access.
+// In the normal build the checks compile to nothing.
+#ifdef BM_CHECKED
+__device__ __forceinline__ bool idx_ok(const Params& p, long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    if (p.chk) atomicCAS(p.chk, 0, -11 /*BM_ERR_CHECK*/);
+    return false;
+}
+#else
+__device__ __forceinline__ bool idx_ok(const Params&, long long, long long) { return true; }
+#endif
 
 // CSR reads: through the read-only (non-coherent) path when the CSR cannot
 // change during the kernel (NC), else through L2 only.
@@ -317,6 +334,7 @@ __device__ __forceinline__ void step_init(const Params& p, int2* q, int slot, Co
         const int c = base + threadIdx.x;
         if (c < nc) {
             int r = __ldcg(&p.cmatch[c]);
+            if (r >= 0 && !idx_ok(p, r, p.nr)) r = -1;
             if (r >= 0 && __ldcg(&p.rmatch[r]) != c) {
                 __stcg(&p.cmatch[c], -1);
                 r = -1;
@@ -361,7 +379,7 @@ __device__ __forceinline__ void step_next_roots(const Params& p, const int2* q, 
         for (int u = 0; u < 4; ++u) c[u] = i0 + u * nthr < tail ? __ldcg(&q[i0 + u * nthr]).x : -1;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            if (c[u] < 0) continue;
+            if (c[u] < 0 || !idx_ok(p, c[u], p.nc)) continue;
             __stcg(&p.level[c[u]], L0 - 1);
             if (WR) __stcg(&p.root[c[u]], -1);
         }
@@ -373,6 +391,7 @@ __device__ __forceinline__ void step_next_roots(const Params& p, const int2* q, 
         for (int u = 0; u < 4; ++u) {
             const int i = base + u * T + threadIdx.x;
             c[u] = i < n_roots ? __ldcg(&q[i]).x : -1;
+            if (c[u] >= 0 && !idx_ok(p, c[u], p.nc)) c[u] = -1;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) m[u] = c[u] >= 0 ? __ldcg(&p.cmatch[c[u]]) : 0;
@@ -413,9 +432,13 @@ __device__ __forceinline__ void tile_load(const Params& p, const int2* queue, in
         const int2 ent = __ldcg(&queue[qb + i]);
         c = ent.x;
         myroot = ent.y;
-        beg = ld_csr<NC>(&p.col_ptr[c]);
-        deg = ld_csr<NC>(&p.col_ptr[c + 1]) - beg;
-        if (WR) rlev = __ldcg(&p.level[myroot]);
+        if (!idx_ok(p, c, p.nc) || (WR && !idx_ok(p, myroot, p.nc))) {  // checked build only
+            c = -1;
+        } else {
+            beg = ld_csr<NC>(&p.col_ptr[c]);
+            deg = ld_csr<NC>(&p.col_ptr[c + 1]) - beg;
+            if (WR) rlev = __ldcg(&p.level[myroot]);
+        }
     }
     if (t == 0 && tile_ctr) sm.tile = (ctr_base < 0 ? (int)gridDim.x : ctr_base) + atomicAdd(tile_ctr, grab);
     const int off = block_exclusive_scan(deg, sm);
@@ -445,6 +468,7 @@ __device__ __forceinline__ void tile_load2(const Params& p, const int2* queue, i
             const int2 ent = __ldcg(&queue[qb + i]);
             c[u] = ent.x;
             rt[u] = ent.y;
+            if (!idx_ok(p, c[u], p.nc) || (WR && !idx_ok(p, rt[u], p.nc))) c[u] = -1;
         }
     }
 #pragma unroll
@@ -504,6 +528,7 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
                 if (sm.col[lo] >= 0) {
                     own[u] = lo;
                     r[u] = ld_csr<NC>(&p.row_idx[sm.beg[lo] + (e - sm.off[lo])]);
+                    if (!idx_ok(p, r[u], p.nr)) own[u] = r[u] = -1;
                 }
             }
         }
@@ -518,10 +543,16 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
                     lv[u] = atomicMax(&p.rvis[r[u]], stamp);
                 }
             }
+#pragma unroll
+            for (int u = 0; u < ILP; ++u)
+                if (cm[u] >= 0 && !idx_ok(p, cm[u], p.nc)) cm[u] = -3;  // checked build only
         } else {
 #pragma unroll
             for (int u = 0; u < ILP; ++u)
                 cm[u] = (own[u] >= 0) ? (CA ? __ldca(&p.rmatch[r[u]]) : __ldcg(&p.rmatch[r[u]])) : -3;
+#pragma unroll
+            for (int u = 0; u < ILP; ++u)
+                if (cm[u] >= 0 && !idx_ok(p, cm[u], p.nc)) cm[u] = -3;  // checked build only
 #pragma unroll
             for (int u = 0; u < ILP; ++u)
                 lv[u] = (cm[u] >= 0 && !direct) ? (CA ? __ldca(&p.level[cm[u]]) : __ldcg(&p.level[cm[u]])) : L0 - 1;
@@ -645,9 +676,11 @@ __device__ __forceinline__ void step_alternate(const Params& p, int n_ep, int ca
         int steps = 0;
         while (r != -1) {
             if (++steps > cap) { set_error(p.ctl, -4 /*BM_ERR_ITER_LIMIT*/); break; }
+            if (!idx_ok(p, r, p.nr)) break;
             const int c = __ldcg(&p.pred[r]);
             if ((unsigned)c >= (unsigned)p.nc) { set_error(p.ctl, -7 /*BM_ERR_STATE*/); break; }
             const int r2 = ld_volatile(&p.cmatch[c]);
+            if (r2 >= 0 && !idx_ok(p, r2, p.nr)) break;
             if (r2 >= 0 && __ldcg(&p.pred[r2]) == c) break;
             st_volatile(&p.cmatch[c], r);
             __stcg(&p.rmatch[r], c);
@@ -670,6 +703,7 @@ __device__ __forceinline__ void step_alternate_disjoint(const Params& p, int n_e
     unsigned steps_done = 0;
     for (int i = tid; i < n_ep; i += nthr) {
         int r = __ldcg(&p.endpoints[i]);
+        if (!idx_ok(p, r, p.nr)) continue;
         int c = __ldcg(&p.pred[r]);
         int steps = 0;
         for (;;) {
@@ -680,6 +714,7 @@ __device__ __forceinline__ void step_alternate_disjoint(const Params& p, int n_e
             __stcg(&p.rmatch[r], c);
             ++steps_done;
             if (rec.y < 0) break;  // c was the root
+            if (!idx_ok(p, rec.y, p.nr)) break;
             r = rec.y;
             c = rec.x;
         }
@@ -698,7 +733,7 @@ __device__ __forceinline__ void step_fix_rows(const Params& p, Counters& cnt) {
     for (int r = tid; r < p.nr; r += nthr) {
         const int m = __ldcg(&p.rmatch[r]);
         if (m == -1) continue;
-        if (m < 0 || __ldcg(&p.cmatch[m]) != r) {
+        if (m < 0 || !idx_ok(p, m, p.nc) || __ldcg(&p.cmatch[m]) != r) {
             __stcg(&p.rmatch[r], -1);
             ++fixes;
         }
@@ -706,11 +741,32 @@ __device__ __forceinline__ void step_fix_rows(const Params& p, Counters& cnt) {
     add_to_counter(&p.ctl->fix_repairs, fixes);
 }
 
+// Range-checked build: between phases the matching must be consistent --
+// every matched row's column points back to it and the other way round.
+// A violation records BM_ERR_CHECK.
+__device__ __forceinline__ void step_check_matching(const Params& p) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthr = gridDim.x * blockDim.x;
+    bool bad = false;
+    for (int r = tid; r < p.nr; r += nthr) {
+        const int m = __ldcg(&p.rmatch[r]);
+        if (m != -1 && (m < 0 || m >= p.nc || __ldcg(&p.cmatch[m]) != r)) bad = true;
+    }
+    for (int c = tid; c < p.nc; c += nthr) {
+        const int m = __ldcg(&p.cmatch[c]);
+        if (m != -1 && (m < 0 || m >= p.nr || __ldcg(&p.rmatch[m]) != c)) bad = true;
+    }
+    if (bad && p.chk) atomicCAS(p.chk, 0, -11 /*BM_ERR_CHECK*/);
+}
+
 // Gives back the rows a BFS-only pass claimed (inspection entry point).
 __device__ __forceinline__ void step_release_endpoints(const Params& p, int n_ep) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthr = gridDim.x * blockDim.x;
-    for (int i = tid; i < n_ep; i += nthr) __stcg(&p.rmatch[__ldcg(&p.endpoints[i])], -1);
+    for (int i = tid; i < n_ep; i += nthr) {
+        const int r = __ldcg(&p.endpoints[i]);
+        if (idx_ok(p, r, p.nr)) __stcg(&p.rmatch[r], -1);
+    }
 }
 
 // ------------------------------------------------------------------ one graph, one block
@@ -731,6 +787,7 @@ __device__ __forceinline__ void block_full_init(const Params& p, Smem& sm, Count
         for (int u = 0; u < 4; ++u) {
             c[u] = base + u * T + t;
             r[u] = c[u] < nc ? __ldcg(&p.cmatch[c[u]]) : -3;
+            if (r[u] >= 0 && !idx_ok(p, r[u], p.nr)) r[u] = -1;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -895,9 +952,11 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
             int steps = 0;
             while (r != -1) {
                 if (++steps > tail + 2) { atomicCAS(&sm.ok, 0, -4); break; }
+                if (!idx_ok(p, r, nr)) { atomicCAS(&sm.ok, 0, -11); break; }
                 const int c = __ldcg(&p.pred[r]);
                 if ((unsigned)c >= (unsigned)nc) { atomicCAS(&sm.ok, 0, -7); break; }
                 const int r2 = ld_volatile(&p.cmatch[c]);
+                if (r2 >= 0 && !idx_ok(p, r2, nr)) { atomicCAS(&sm.ok, 0, -11); break; }
                 if (r2 >= 0 && __ldcg(&p.pred[r2]) == c) break;
                 st_volatile(&p.cmatch[c], r);
                 __stcg(&p.rmatch[r], c);
@@ -911,6 +970,7 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
             // columns inserted by this search go back to "unvisited" ...
             for (int i = n_roots + t; i < tail; i += T) {
                 const int c = __ldcg(&p.queue[i]).x;
+                if (!idx_ok(p, c, nc)) continue;
                 __stcg(&p.level[c], L0 - 1);
                 if (WR) __stcg(&p.root[c], -1);
             }
@@ -922,6 +982,7 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
                 int c = -1, keep = 0;
                 if (i < n_roots) {
                     c = __ldcg(&p.queue[i]).x;
+                    if (!idx_ok(p, c, nc)) c = 0;  // checked build only: recorded, and column 0 is harmless here
                     keep = __ldcg(&p.cmatch[c]) < 0;
                     if (!keep) {
                         __stcg(&p.level[c], L0 - 1);

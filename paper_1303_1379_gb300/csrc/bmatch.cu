@@ -159,6 +159,11 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
             step_next_roots<WR>(p, qcur, n_roots, tail, qnext, s3 % 3, sm);
             if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
             n_roots = sm.bc_a;
+#ifdef BM_CHECKED
+            step_check_matching(p);
+            if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, &ctl->err)) goto out;
+            if (sm.bc_c != 0) goto out;
+#endif
             card = p.nc - (iso_free + n_roots);
             int2* t = qcur;
             qcur = qnext;
@@ -176,6 +181,11 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
             if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, &ctl->ecnt[s % 3])) goto out;
             n_roots = sm.bc_a;
             card = p.nc - sm.bc_c;
+#ifdef BM_CHECKED
+            step_check_matching(p);
+            if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, &ctl->err)) goto out;
+            if (sm.bc_c != 0) goto out;
+#endif
         }
     }
 out:
@@ -567,6 +577,7 @@ Params make_params(bm_ctx* ctx, bool bfs_only) {
     p.bfs_only = bfs_only ? 1 : 0;
     p.profile = ctx->profile;
     p.profile_cap = kProfileCap;
+    p.chk = &ctx->ctl->err;
     p.wait_ns = ctx->opt.wait_timeout_ns ? ctx->opt.wait_timeout_ns : 5000000000LL;
     p.total_ns = ctx->opt.total_timeout_ns ? ctx->opt.total_timeout_ns : 120000000000LL;
     return p;
@@ -774,6 +785,7 @@ const char* bm_status_string(int32_t s) {
         case BM_ERR_UNSUPPORTED: return "device cannot run the cooperative launch";
         case BM_ERR_INVALID_MATCHING: return "initial matching out of range or rmatch/cmatch not inverse";
         case BM_ERR_TOO_LARGE: return "graph too large for the allocation-free entry point's scratch";
+        case BM_ERR_CHECK: return "range-checked build: an index out of range or an inconsistent matching";
         default: return "unknown status";
     }
 }
@@ -1187,6 +1199,7 @@ extern "C" int32_t bm_match_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
     p.queue = (int2*)(s + off_q);
     p.endpoints = (int32_t*)(s + off_ep);
     p.ctl = ctl;
+    p.chk = &ctl->err;
     p.mode = BM_APFB;
     p.one_ep = 1;
     p.max_phases = (n_rows < n_cols ? n_rows : n_cols) + 2;
@@ -1300,6 +1313,7 @@ int32_t bmi::enqueue_match(bmd::Params p, long long nnz, bool wr, int greedy, cu
     p.bfs_only = 0;
     p.profile = nullptr;
     p.profile_cap = 0;
+    p.chk = &p.ctl->err;
     p.max_phases = (p.nr < p.nc ? p.nr : p.nc) + 2;
     p.phase_limit_is_error = 1;
     p.stamp_base = 0;  // the stamps were just cleared

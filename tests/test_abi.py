@@ -36,9 +36,23 @@ def test_library_exports_every_declared_symbol():
     assert set(bmatch.EXPORTS) <= set(names)
 
 
+def test_checked_library_exports_the_same_symbols():
+    """The range-checked twin (BM_CHECKED) is built beside the library and
+    exports the same entry points, so BMATCH_CHECKED=1 can swap it in."""
+    build.build(checked=True)
+    assert os.path.exists(build.LIB_CHECKED)
+    names = declared_functions()
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB_CHECKED], capture_output=True, text=True)
+    if out.returncode == 0:
+        assert set(names) <= set(re.findall(r"\sT\s+(\w+)", out.stdout))
+    lib = ctypes.CDLL(build.LIB_CHECKED)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
 def test_status_strings_and_defaults():
     assert bmatch.status_string(0) == "ok"
-    for code in range(-9, 2):
+    for code in range(-11, 2):
         assert bmatch.status_string(code) != "unknown status"
     o = bmatch.default_options()
     assert (o.mode, o.bfs, o.driver, o.wr_one_endpoint, o.max_phases) == (0, 1, 0, 1, 0)
