@@ -187,6 +187,21 @@ BM_API int32_t bm_match(bm_ctx *ctx, int32_t *rmatch_out, int32_t *cmatch_out, i
                  bm_stats *stats);
 
 /*
+ * bm_set_matching + bm_match in one call: installs the initial matching
+ * rmatch0 (n_rows) / cmatch0 (n_cols) (device arrays, copied; checked as by
+ * bm_set_matching; Section 3: the method starts from any matching held in
+ * rmatch / cmatch) and runs Algorithm 1 from it, with one host
+ * synchronisation at the end instead of two (the match launch returns at
+ * once when the check failed).  Restarting from a saved matching -- resuming,
+ * or timing repeated runs -- takes this call.  Outputs as for bm_match.  An
+ * invalid initial matching returns BM_ERR_INVALID_MATCHING and leaves the
+ * empty matching installed; the context stays usable.
+ */
+BM_API int32_t bm_match_from(bm_ctx *ctx, const int32_t *rmatch0, const int32_t *cmatch0,
+                             int32_t *rmatch_out, int32_t *cmatch_out, int32_t *card_out,
+                             bm_stats *stats);
+
+/*
  * One-shot call with HOST buffers: copies the CSR (h_col_ptr, h_row_idx) and
  * the initial matching (h_rmatch, h_cmatch; both NULL = empty) to the device,
  * runs bm_match, and writes the maximum matching back into h_rmatch/h_cmatch

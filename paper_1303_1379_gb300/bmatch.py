@@ -83,7 +83,7 @@ class bm_batch_stats(ctypes.Structure):
 
 EXPORTS = ("bm_default_options", "bm_version", "bm_status_string", "bm_create", "bm_upload_csr",
            "bm_set_options", "bm_greedy", "bm_set_matching", "bm_get_matching", "bm_match",
-           "bm_match_host", "bm_bfs", "bm_phase_profile", "bm_destroy", "bm_batch_create",
+           "bm_match_host", "bm_match_from", "bm_bfs", "bm_phase_profile", "bm_destroy", "bm_batch_create",
            "bm_batch_set_options", "bm_batch_match", "bm_batch_graph_status", "bm_batch_autotune",
            "bm_batch_destroy", "bm_match_noalloc", "bm_server_default_options", "bm_server_create",
            "bm_server_submit", "bm_server_poll", "bm_server_wait", "bm_server_cancel",
@@ -167,6 +167,8 @@ def load(build_if_missing: bool = True):
             lib.bm_match.restype = ctypes.c_int32
             lib.bm_match_host.argtypes = [VP, VP, VP, VP, VP, I32P, ctypes.POINTER(bm_stats)]
             lib.bm_match_host.restype = ctypes.c_int32
+            lib.bm_match_from.argtypes = [VP, VP, VP, VP, VP, I32P, ctypes.POINTER(bm_stats)]
+            lib.bm_match_from.restype = ctypes.c_int32
             lib.bm_bfs.argtypes = [VP, VP, VP, VP, VP, I32P]
             lib.bm_bfs.restype = ctypes.c_int32
             lib.bm_phase_profile.argtypes = [VP, ctypes.c_int32, I32P, I32P, I32P, I32P, I32P]
@@ -343,6 +345,15 @@ class Matcher:
         rc = self._lib.bm_match(self._h, _ptr(rmatch_out), _ptr(cmatch_out), ctypes.byref(card),
                                 ctypes.byref(st))
         _check(rc, "bm_match", (BM_OK, BM_INCOMPLETE) if allow_incomplete else (BM_OK,))
+        return MatchResult(rc, card.value, st.as_dict())
+
+    def match_from(self, rmatch0, cmatch0, rmatch_out=None, cmatch_out=None) -> MatchResult:
+        """bm_match_from: install (rmatch0, cmatch0) and match, one host sync."""
+        card = ctypes.c_int32(0)
+        st = bm_stats()
+        rc = self._lib.bm_match_from(self._h, _ptr(rmatch0), _ptr(cmatch0), _ptr(rmatch_out),
+                                     _ptr(cmatch_out), ctypes.byref(card), ctypes.byref(st))
+        _check(rc, "bm_match_from")
         return MatchResult(rc, card.value, st.as_dict())
 
     def match_host(self, h_col_ptr, h_row_idx, h_rmatch=None, h_cmatch=None) -> MatchResult:

@@ -992,6 +992,32 @@ int32_t bm_match(bm_ctx* ctx, int32_t* rmatch_out, int32_t* cmatch_out, int32_t*
     return finish(ctx, card_out, stats);
 }
 
+int32_t bm_match_from(bm_ctx* ctx, const int32_t* rmatch0, const int32_t* cmatch0, int32_t* rmatch_out,
+                      int32_t* cmatch_out, int32_t* card_out, bm_stats* stats) {
+    if (!ctx || !rmatch0 || !cmatch0) return BM_ERR_INVALID_ARG;
+    if (ctx->sticky || !ctx->csr_ready) return BM_ERR_STATE;
+    cudaStream_t st = ctx->stream;
+    BM_CUDA(ctx, cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), st));
+    if (ctx->nr) BM_CUDA(ctx, cudaMemcpyAsync(ctx->rmatch, rmatch0, 4 * (size_t)ctx->nr, cudaMemcpyDeviceToDevice, st));
+    if (ctx->nc) BM_CUDA(ctx, cudaMemcpyAsync(ctx->cmatch, cmatch0, 4 * (size_t)ctx->nc, cudaMemcpyDeviceToDevice, st));
+    // the check reports through the control block; the match launch then returns at once
+    k_check_matching<<<grid_for(ctx, ctx->nr > ctx->nc ? ctx->nr : ctx->nc), ctx->block, 0, st>>>(
+        ctx->nr, ctx->nc, ctx->rmatch, ctx->cmatch, ctx->ctl);
+    BM_CUDA(ctx, cudaGetLastError());
+    int32_t rc = run(ctx, false);
+    if (rc < 0) return rc;
+    if (rmatch_out && ctx->nr) BM_CUDA(ctx, cudaMemcpyAsync(rmatch_out, ctx->rmatch, 4 * (size_t)ctx->nr, cudaMemcpyDeviceToDevice, st));
+    if (cmatch_out && ctx->nc) BM_CUDA(ctx, cudaMemcpyAsync(cmatch_out, ctx->cmatch, 4 * (size_t)ctx->nc, cudaMemcpyDeviceToDevice, st));
+    rc = finish(ctx, card_out, stats);
+    if (rc == BM_ERR_INVALID_MATCHING) {
+        ctx->sticky = 0;  // bad input is not a broken context: leave the empty matching installed
+        cudaMemsetAsync(ctx->rmatch, 0xff, 4 * (size_t)ctx->nr, st);
+        cudaMemsetAsync(ctx->cmatch, 0xff, 4 * (size_t)ctx->nc, st);
+        cudaStreamSynchronize(st);
+    }
+    return rc;
+}
+
 int32_t bm_match_host(bm_ctx* ctx, const int32_t* h_col_ptr, const int32_t* h_row_idx,
                       int32_t* h_rmatch, int32_t* h_cmatch, int32_t* card_out, bm_stats* stats) {
     if (!ctx || !h_col_ptr || (!h_row_idx && ctx->nnz > 0) || ((h_rmatch == nullptr) != (h_cmatch == nullptr)))

@@ -333,6 +333,33 @@ def test_gpu_greedy_passes_are_maximal(gname):
     assert res.card == oracle_max(g)
 
 
+def test_match_from_equals_set_matching_then_match():
+    """bm_match_from (install + Algorithm 1, one host sync) gives the same |M|
+    as bm_set_matching + bm_match, leaves a valid maximum matching, rejects an
+    invalid start without breaking the context, and restarts cleanly."""
+    g = synth.rmat_graph(16, 1 << 20, seed=4)
+    want = oracle_max(g)
+    rm0, cm0, _ = oracle.greedy(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+    cp, ri = to_dev(g)
+    d_rm0, d_cm0 = torch.from_numpy(rm0).cuda(), torch.from_numpy(cm0).cuda()
+    rm = torch.empty(g.n_rows, dtype=torch.int32, device="cuda")
+    cm = torch.empty(g.n_cols, dtype=torch.int32, device="cuda")
+    with bmatch.Matcher(g.n_rows, g.n_cols, g.nnz, cp, ri) as m:
+        m.set_matching(d_rm0, d_cm0)
+        a = m.match()
+        for _ in range(2):  # twice in a row from the same start
+            b = m.match_from(d_rm0, d_cm0, rm, cm)
+            assert a.card == b.card == want
+            assert b.stats["initial_card"] == int((cm0 >= 0).sum())
+            assert_maximum(g, rm.cpu().numpy(), cm.cpu().numpy(), b.card, want)
+        bad = rm0.copy()
+        bad[int(np.flatnonzero(rm0 >= 0)[0])] = -1  # one row forgets its column
+        with pytest.raises(bmatch.BMError) as e:
+            m.match_from(torch.from_numpy(bad).cuda(), d_cm0)
+        assert e.value.status == bmatch.BM_ERR_INVALID_MATCHING
+        assert m.match_from(d_rm0, d_cm0).card == want  # the context is still usable
+
+
 def test_phase_limit_gives_valid_partial_matchings(c1):
     cards = []
     for k in (1, 2, 3):
