@@ -106,15 +106,19 @@ def _code_only(text: str) -> str:
 
 def source_hash(kernel: str = "k_match") -> str:
     """Hash of the code that makes up a kernel, comments and whitespace
-    excluded: the device header plus the persistent matching kernel's body
-    (k_match; other kernels in that file do not change it) or the whole
-    batched-path source (k_batch)."""
+    excluded: the device header plus the kernel's own part of its source file
+    (the persistent matching kernel's body for k_match, the batched kernel
+    with its parameter structs for k_batch); host code and other kernels in
+    those files do not change it."""
     h = hashlib.sha256()
     with open(os.path.join(ROOT, "paper_1303_1379_gb300/csrc/bm_device.cuh"), "r") as fh:
         h.update(_code_only(fh.read()).encode())
     if kernel == "k_batch":
         with open(os.path.join(ROOT, "paper_1303_1379_gb300/csrc/bm_batch.cu"), "r") as fh:
-            h.update(_code_only(fh.read()).encode())
+            text = fh.read()
+        start = text.find("struct alignas(128) BatchCtl")
+        end = text.find("// Validates every graph's local CSR")
+        h.update(_code_only(text[start:end]).encode())
         return h.hexdigest()[:16]
     with open(os.path.join(ROOT, "paper_1303_1379_gb300/csrc/bmatch.cu"), "r") as fh:
         text = fh.read()

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "bm_device.cuh"
+#include "bm_internal.h"
 #include "bmatch.h"
 
 using bmd::Counters;
@@ -260,6 +261,7 @@ int32_t capture(bm_batch* b, int32_t* rmatch, int32_t* cmatch, int greedy) {
 extern "C" {
 
 int32_t bm_batch_create(const bm_batch_desc* desc, void* stream, const bm_options* opt, bm_batch** out) {
+    bmi::NvtxRange nvtx_range("bm_batch_create");
     if (!out || !desc) return BM_ERR_INVALID_ARG;
     *out = nullptr;
     const int G = desc->n_graphs;
@@ -380,6 +382,7 @@ int32_t bm_batch_set_options(bm_batch* b, const bm_options* opt) {
 
 int32_t bm_batch_match(bm_batch* b, int32_t greedy, int32_t* rmatch, int32_t* cmatch, int32_t* card_out,
                        bm_batch_stats* stats) {
+    bmi::NvtxRange nvtx_range("bm_batch_match");
     if (!b || ((!rmatch || !cmatch) && b->d.n_graphs > 0)) return BM_ERR_INVALID_ARG;
     if (b->sticky) return BM_ERR_STATE;
     cudaStream_t st = b->stream;
@@ -441,6 +444,7 @@ extern "C" int32_t bm_batch_autotune(bm_batch* b, int32_t greedy, const int32_t*
                                      int32_t* rmatch_work, int32_t* cmatch_work, int32_t n_candidates,
                                      const int32_t* block_sizes, const int32_t* blocks_per_sm, int32_t reps,
                                      float* ms_out, int32_t* best_out) {
+    bmi::NvtxRange nvtx_range("bm_batch_autotune");
     if (!b || !block_sizes || !blocks_per_sm || !best_out || n_candidates < 1 || reps < 1) return BM_ERR_INVALID_ARG;
     if (b->d.n_graphs > 0 && (!rmatch0 || !cmatch0 || !rmatch_work || !cmatch_work)) return BM_ERR_INVALID_ARG;
     if (b->sticky) return BM_ERR_STATE;

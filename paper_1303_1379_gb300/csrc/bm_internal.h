@@ -2,11 +2,23 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstdint>
 
 #include "bm_device.cuh"
 
 namespace bmi {
+
+// NVTX range over one C-ABI call (header-only NVTX: free unless a profiler
+// that reads NVTX is attached), so that timelines show which call launched
+// which kernels.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Enqueues on `st`, without waiting, the whole method on one graph over the
 // whole GPU (the persistent single-graph kernel):

@@ -602,6 +602,7 @@ int32_t bm_server_create(const bm_server_options* opt, bm_server** out) {
 
 int32_t bm_server_submit(bm_server* s, int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* h_col_ptr,
                          const int32_t* h_row_idx, int32_t greedy, int64_t* id_out) {
+    bmi::NvtxRange nvtx_range("bm_server_submit");
     if (!s || !id_out || n_rows < 0 || n_cols < 0 || nnz < 0 || nnz > 0x7fffffffLL || !h_col_ptr ||
         (!h_row_idx && nnz > 0))
         return BM_ERR_INVALID_ARG;
@@ -639,6 +640,7 @@ int32_t bm_server_poll(bm_server* s, int64_t id, bm_request_info* info) {
 }
 
 int32_t bm_server_wait(bm_server* s, int64_t id, int64_t timeout_ns, bm_request_info* info) {
+    bmi::NvtxRange nvtx_range("bm_server_wait");
     if (!s || !info) return BM_ERR_INVALID_ARG;
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->reqs.find(id);

@@ -792,6 +792,7 @@ const char* bm_status_string(int32_t s) {
 
 int32_t bm_create(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* col_ptr,
                   const int32_t* row_idx, void* stream, const bm_options* opt, bm_ctx** out) {
+    bmi::NvtxRange nvtx_range("bm_create");
     if (!out) return BM_ERR_INVALID_ARG;
     *out = nullptr;
     if (n_rows < 0 || n_cols < 0 || nnz < 0 || nnz > 0x7fffffffLL) return BM_ERR_INVALID_ARG;
@@ -911,6 +912,7 @@ int32_t bm_set_options(bm_ctx* ctx, const bm_options* opt) {
 }
 
 int32_t bm_upload_csr(bm_ctx* ctx, const int32_t* h_col_ptr, const int32_t* h_row_idx) {
+    bmi::NvtxRange nvtx_range("bm_upload_csr");
     if (!ctx || !h_col_ptr || (!h_row_idx && ctx->nnz > 0)) return BM_ERR_INVALID_ARG;
     if (ctx->sticky || !ctx->owns_csr) return BM_ERR_STATE;
     cudaStream_t st = ctx->stream;
@@ -927,6 +929,7 @@ int32_t bm_upload_csr(bm_ctx* ctx, const int32_t* h_col_ptr, const int32_t* h_ro
 }
 
 int32_t bm_greedy(bm_ctx* ctx, int32_t* card_out) {
+    bmi::NvtxRange nvtx_range("bm_greedy");
     if (!ctx) return BM_ERR_INVALID_ARG;
     if (ctx->sticky || !ctx->csr_ready) return BM_ERR_STATE;
     cudaStream_t st = ctx->stream;
@@ -945,6 +948,7 @@ int32_t bm_greedy(bm_ctx* ctx, int32_t* card_out) {
 }
 
 int32_t bm_set_matching(bm_ctx* ctx, const int32_t* rmatch, const int32_t* cmatch) {
+    bmi::NvtxRange nvtx_range("bm_set_matching");
     if (!ctx || ((rmatch == nullptr) != (cmatch == nullptr))) return BM_ERR_INVALID_ARG;
     if (ctx->sticky) return BM_ERR_STATE;
     cudaStream_t st = ctx->stream;
@@ -981,6 +985,7 @@ int32_t bm_get_matching(bm_ctx* ctx, int32_t* rmatch_out, int32_t* cmatch_out) {
 }
 
 int32_t bm_match(bm_ctx* ctx, int32_t* rmatch_out, int32_t* cmatch_out, int32_t* card_out, bm_stats* stats) {
+    bmi::NvtxRange nvtx_range("bm_match");
     if (!ctx) return BM_ERR_INVALID_ARG;
     if (ctx->sticky || !ctx->csr_ready) return BM_ERR_STATE;
     cudaStream_t st = ctx->stream;
@@ -994,6 +999,7 @@ int32_t bm_match(bm_ctx* ctx, int32_t* rmatch_out, int32_t* cmatch_out, int32_t*
 
 int32_t bm_match_from(bm_ctx* ctx, const int32_t* rmatch0, const int32_t* cmatch0, int32_t* rmatch_out,
                       int32_t* cmatch_out, int32_t* card_out, bm_stats* stats) {
+    bmi::NvtxRange nvtx_range("bm_match_from");
     if (!ctx || !rmatch0 || !cmatch0) return BM_ERR_INVALID_ARG;
     if (ctx->sticky || !ctx->csr_ready) return BM_ERR_STATE;
     cudaStream_t st = ctx->stream;
@@ -1020,6 +1026,7 @@ int32_t bm_match_from(bm_ctx* ctx, const int32_t* rmatch0, const int32_t* cmatch
 
 int32_t bm_match_host(bm_ctx* ctx, const int32_t* h_col_ptr, const int32_t* h_row_idx,
                       int32_t* h_rmatch, int32_t* h_cmatch, int32_t* card_out, bm_stats* stats) {
+    bmi::NvtxRange nvtx_range("bm_match_host");
     if (!ctx || !h_col_ptr || (!h_row_idx && ctx->nnz > 0) || ((h_rmatch == nullptr) != (h_cmatch == nullptr)))
         return BM_ERR_INVALID_ARG;
     if (ctx->sticky || !ctx->owns_csr) return BM_ERR_STATE;
@@ -1066,6 +1073,7 @@ int32_t bm_match_host(bm_ctx* ctx, const int32_t* h_col_ptr, const int32_t* h_ro
 
 int32_t bm_bfs(bm_ctx* ctx, int32_t* level_out, int32_t* root_out, int32_t* pred_out,
                int32_t* endpoints_out, int32_t* n_endpoints_out) {
+    bmi::NvtxRange nvtx_range("bm_bfs");
     if (!ctx) return BM_ERR_INVALID_ARG;
     if (ctx->sticky || !ctx->csr_ready) return BM_ERR_STATE;
     cudaStream_t st = ctx->stream;
@@ -1190,6 +1198,7 @@ extern "C" int32_t bm_match_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
                                     const int32_t* col_ptr, const int32_t* row_idx,
                                     int32_t* rmatch, int32_t* cmatch, void* stream,
                                     int32_t* card_out) {
+    bmi::NvtxRange nvtx_range("bm_match_noalloc");
     if (n_rows < 0 || n_cols < 0 || nnz < 0 || nnz > 0x7fffffffLL) return BM_ERR_INVALID_ARG;
     if (!col_ptr || (!row_idx && nnz > 0) || (!rmatch && n_rows > 0) || (!cmatch && n_cols > 0))
         return BM_ERR_INVALID_ARG;
