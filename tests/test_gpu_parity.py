@@ -150,6 +150,32 @@ def test_gpubfs_levels_equal_alternating_bfs_wide(gname, driver):
             assert any(32768 < x <= one_tile_per_block for x in w), (widths, one_tile_per_block)
 
 
+@pytest.mark.parametrize("gname", ["uniform", "rmat", "stencil"])
+@pytest.mark.parametrize("driver", [0, 1], ids=["persistent", "host"])
+def test_apsb_gpubfs_stops_after_the_first_level_with_an_endpoint(gname, driver):
+    """APsB (Algorithm 1's break): the search expands levels L0, L0 + 1, ...
+    until the first level k* whose columns reach an unmatched row, completes
+    that level and stops.  So exactly the columns at alternating distance
+    <= k* + 1 - L0 are reached, at their distance, and the endpoints are the
+    unmatched rows adjacent to the columns of level k* (reading 11)."""
+    g = {"uniform": lambda: synth.uniform_graph(20011, 19993, 6, seed=4),
+         "rmat": lambda: synth.rmat_graph(15, 200000, seed=5),
+         "stencil": lambda: synth.stencil_graph(150, 2250, 0.05, seed=6)}[gname]()
+    rm0, cm0, _ = oracle.greedy(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+    full, _ = oracle.bfs_levels(g.n_rows, g.n_cols, g.col_ptr, g.row_idx, rm0, cm0, L0=2)
+    deg = np.diff(g.col_ptr)
+    col_of_edge = np.repeat(np.arange(g.n_cols), deg)
+    free_edge = rm0[g.row_idx] == -1
+    # the first frontier level that touches an unmatched row
+    touching = np.unique(full[col_of_edge[free_edge]])
+    kstar = int(touching[touching >= 2].min())
+    want_level = np.where((full >= 2) & (full <= kstar + 1), full, 1)
+    want_ends = np.unique(g.row_idx[free_edge & (full[col_of_edge] == kstar)])
+    level, root, pred, ends = bfs_gpu(g, (rm0, cm0), mode=1, bfs=0, driver=driver)
+    assert np.array_equal(level, want_level)
+    assert np.array_equal(np.sort(ends), want_ends)
+
+
 @pytest.mark.parametrize("one_ep", [1, 0])
 def test_gpubfs_wr_trees_are_valid(one_ep):
     """GPUBFS-WR trees depend on timing; check what must hold: levels never
