@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--extra-workloads", default="stencil2000,uniform10k",
                     help="workloads measured beside the main one (comma list, empty for none)")
     ap.add_argument("--extra-steps", type=int, default=5)
+    ap.add_argument("--serve-exclusive-alongside", type=int, default=None,
+                    help="1: large requests run beside the workers instead of alone (default: the library's)")
     ap.add_argument("--serve-exclusive-min-edges", type=int, default=None,
                     help="requests with at least this many edges run alone on the whole GPU "
                          "(0 = never; default: the library's)")
@@ -508,6 +510,8 @@ def bench_serving(args, torch, bmatch):
     mean_edges = float(np.mean([h[4] for h in host]))
     deal = shard.assign_stream([host[i % len(host)][4] for i in range(N)], world)
     sopts = {} if args.serve_exclusive_min_edges is None else {"exclusive_min_edges": args.serve_exclusive_min_edges}
+    if args.serve_exclusive_alongside is not None:
+        sopts["exclusive_alongside"] = args.serve_exclusive_alongside
     srv = bmatch.Server(pool_bytes=32 << 30, **sopts)
 
     def run(rate):
@@ -552,6 +556,7 @@ def bench_serving(args, torch, bmatch):
             raise SystemExit("served results differ between runs")
     st = srv.stats()
     srv_opts_threshold = srv.options.exclusive_min_edges
+    srv_alongside = srv.options.exclusive_alongside
     srv.close()
     distinct = {}
     for i, c in enumerate(cards[:len(host)]):
@@ -584,6 +589,7 @@ def bench_serving(args, torch, bmatch):
             "requests_per_run": N, "mean_edges_per_request": mean_edges, "generate_s": round(t_gen, 1),
             "lambda_max_rps": lam, "runs": runs, "worker_grid": st["grid"], "worker_block": st["block"],
             "exclusive_min_edges": int(srv_opts_threshold), "requests_run_alone": int(st["exclusive_runs"]),
+            "exclusive_alongside": int(srv_alongside),
             "one_by_one": one, "one_by_one_rps": one["rps"],
             "speedup_vs_one_by_one": lam / one["rps"] if one["rps"] else None,
             "parallelism": f"stream dealt by request over {world} ranks" if world > 1 else "single GPU",

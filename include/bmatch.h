@@ -339,17 +339,22 @@ typedef struct bm_server_options {
     int64_t reserve_bytes;   /* left free when pool_bytes = 0 (default 2 GiB)                    */
     int32_t ring_slots;      /* requests admitted at once (default 1024)                         */
     int32_t block_size;      /* threads per worker block (default 512)                           */
-    int32_t blocks_per_sm;   /* worker blocks per SM (default 2, capped by occupancy)            */
+    int32_t blocks_per_sm;   /* worker blocks per SM (default 2, capped by occupancy; 1 with
+                                exclusive_alongside)                                          */
     int32_t mode;            /* BM_APFB (default) / BM_APSB                                      */
     int32_t bfs;             /* BM_GPUBFS_WR (default) / BM_GPUBFS                               */
     int32_t keep_results;    /* 1: keep each request's matching until bm_server_release          */
     int64_t idle_timeout_ns; /* workers leave when no block has been busy this long (default 50 ms) */
     int32_t poll_interval_us;/* scheduler sleep when idle (default 5)                             */
-    int32_t reserved0;
-    int64_t exclusive_min_edges; /* requests with at least this many edges run alone on the whole
-                                    GPU (the single-graph persistent kernel, after the workers
-                                    leave; consecutive ones back to back) instead of on one
-                                    worker block; 0 = never (default 262,144)                 */
+    int32_t exclusive_alongside; /* 1 (default): requests of at least exclusive_min_edges run on
+                                    their own stream beside the workers (one block per SM each,
+                                    so both stay resident and small requests do not wait behind
+                                    large ones); 0: the workers leave first and the request has
+                                    the whole GPU                                              */
+    int64_t exclusive_min_edges; /* requests with at least this many edges run on the single-graph
+                                    persistent kernel (one after another; beside the workers or
+                                    alone, see exclusive_alongside) instead of on one worker
+                                    block; 0 = never (default 262,144)                        */
     int64_t reserved[3];
 } bm_server_options;
 

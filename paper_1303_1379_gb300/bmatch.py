@@ -39,7 +39,7 @@ class bm_server_options(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("bfs", ctypes.c_int32), ("keep_results", ctypes.c_int32),
                 ("idle_timeout_ns", ctypes.c_int64), ("poll_interval_us", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("exclusive_min_edges", ctypes.c_int64),
+                ("exclusive_alongside", ctypes.c_int32), ("exclusive_min_edges", ctypes.c_int64),
                 ("reserved", ctypes.c_int64 * 3)]
 
 

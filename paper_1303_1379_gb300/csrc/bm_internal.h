@@ -32,6 +32,8 @@ struct NvtxRange {
 // (n_cols), ctl; mode and one_ep select the variant (GPUBFS-WR when wr).
 // The outcome (status, |M|, phases) is in p.ctl when the stream reaches it.
 // Returns BM_OK, or BM_ERR_CUDA / BM_ERR_UNSUPPORTED when a launch failed.
-int32_t enqueue_match(bmd::Params p, long long nnz, bool wr, int greedy, cudaStream_t st);
+// blocks_per_sm > 0 caps the cooperative grid at that many blocks per SM (a
+// launch that shares the GPU with other resident kernels); 0 = as many as fit.
+int32_t enqueue_match(bmd::Params p, long long nnz, bool wr, int greedy, cudaStream_t st, int blocks_per_sm = 0);
 
 }  // namespace bmi

@@ -13,12 +13,16 @@
 // Workers leave after an idle period (every wait is bounded) and the
 // scheduler relaunches them when work is published.
 // A request with at least exclusive_min_edges edges would hold one block for
-// tens of milliseconds; it runs alone on the whole GPU instead: the workers
-// are told to leave (they finish the requests they hold), and the checks,
-// the cheap matching and one launch of the single-graph persistent kernel
-// are queued behind them on the same stream.  Consecutive large requests run
-// back to back behind one departure; the next request for the workers waits
-// until they are done (arrival order).
+// tens of milliseconds; it runs on the single-graph persistent kernel
+// instead.  By default (exclusive_alongside) that launch shares the GPU with
+// the workers: the workers keep one block per SM and the large requests run
+// one after another on their own stream with one block per SM, so both stay
+// resident and small requests do not queue behind large ones.  Otherwise the
+// workers are told to leave (they finish the requests they hold), the checks,
+// the cheap matching and the launch are queued behind them on the same
+// stream, consecutive large requests run back to back behind one departure,
+// and the next request for the workers waits until they are done (arrival
+// order).
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -258,6 +262,7 @@ struct bm_server {
     int grid = 0;
     cudaStream_t copy_stream = nullptr;
     cudaStream_t work_stream = nullptr;
+    cudaStream_t excl_stream = nullptr;  // whole-GPU runs that share the GPU with the workers
     unsigned char* pool = nullptr;
     PoolAllocator* alloc = nullptr;
     void* mapped = nullptr;  // host-mapped: head, desc[ring], done[ring]
@@ -346,12 +351,15 @@ int32_t start_exclusive(bm_server* s, Request& r, int slot) {
     p.ctl = (bmd::Ctl*)(b + offs[12]);
     p.mode = s->opt.mode;
     p.one_ep = 1;
-    __atomic_store_n(&s->head->stop, 1, __ATOMIC_RELEASE);  // workers finish what they hold and leave
-    int32_t rc = bmi::enqueue_match(p, r.nnz, s->opt.bfs == BM_GPUBFS_WR, r.greedy, s->work_stream);
+    // alongside: the launch takes one block per SM beside the workers' one, on its own
+    // stream; otherwise the workers finish what they hold and leave first
+    const bool along = s->opt.exclusive_alongside != 0;
+    if (!along) __atomic_store_n(&s->head->stop, 1, __ATOMIC_RELEASE);
+    cudaStream_t st = along ? s->excl_stream : s->work_stream;
+    int32_t rc = bmi::enqueue_match(p, r.nnz, s->opt.bfs == BM_GPUBFS_WR, r.greedy, st, along ? 1 : 0);
     if (rc != BM_OK) return rc;
-    if (cudaMemcpyAsync(&s->h_excl_ctl[slot], p.ctl, sizeof(bmd::Ctl), cudaMemcpyDeviceToHost, s->work_stream) !=
-            cudaSuccess ||
-        cudaEventRecord(s->excl_ev[slot], s->work_stream) != cudaSuccess) {
+    if (cudaMemcpyAsync(&s->h_excl_ctl[slot], p.ctl, sizeof(bmd::Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaEventRecord(s->excl_ev[slot], st) != cudaSuccess) {
         (void)cudaGetLastError();
         return BM_ERR_CUDA;
     }
@@ -402,7 +410,7 @@ bool schedule_once(bm_server* s) {
         moved = true;
     }
     // with no whole-GPU run queued the workers may run (again); starting one sets stop
-    if (s->excl_runs.empty()) __atomic_store_n(&s->head->stop, 0, __ATOMIC_RELEASE);
+    if (s->excl_runs.empty() && !s->opt.exclusive_alongside) __atomic_store_n(&s->head->stop, 0, __ATOMIC_RELEASE);
     // uploads that finished, in order: publish to the workers, or run alone; a
     // request for the workers waits until the whole-GPU runs ahead of it are done
     while (!s->uploading.empty()) {
@@ -423,7 +431,7 @@ bool schedule_once(bm_server* s) {
             moved = true;
             continue;
         }
-        if (!s->excl_runs.empty()) break;
+        if (!s->excl_runs.empty() && !s->opt.exclusive_alongside) break;
         const int slot = (int)(s->next_ticket % ring);
         if (s->ring_owner[slot] != -1) break;  // ticket next_ticket - ring still running
         const long long ticket = s->next_ticket++;
@@ -487,7 +495,7 @@ bool schedule_once(bm_server* s) {
     // workers: keep one launch alive while requests are published (not while one runs alone)
     bool need = false;
     for (int k = 0; k < ring && !need; ++k) need = s->ring_owner[k] >= 0 && s->reqs[s->ring_owner[k]].state == RUNNING;
-    if (need && s->excl_runs.empty()) {
+    if (need && (s->excl_runs.empty() || s->opt.exclusive_alongside)) {
         const bool alive = s->worker_launched && cudaEventQuery(s->worker_ev) == cudaErrorNotReady;
         if (!alive) launch_workers(s);
     }
@@ -525,6 +533,7 @@ void bm_server_default_options(bm_server_options* o) {
     o->idle_timeout_ns = 50000000;  // 50 ms
     o->poll_interval_us = 5;
     o->exclusive_min_edges = 1 << 18;
+    o->exclusive_alongside = 1;
 }
 
 int32_t bm_server_create(const bm_server_options* opt, bm_server** out) {
@@ -555,7 +564,9 @@ int32_t bm_server_create(const bm_server_options* opt, bm_server** out) {
     }
     if (per_sm < 1) return fail(BM_ERR_UNSUPPORTED);
     s->block = o.block_size;
-    s->grid = s->num_sms * (o.blocks_per_sm < per_sm ? o.blocks_per_sm : per_sm);
+    // alongside: one worker block per SM, leaving the other half of each SM to the whole-GPU lane
+    const int bps = o.exclusive_alongside ? 1 : (o.blocks_per_sm < per_sm ? o.blocks_per_sm : per_sm);
+    s->grid = s->num_sms * bps;
     size_t pool = (size_t)o.pool_bytes;
     if (pool == 0) {
         size_t fr = 0, tot = 0;
@@ -579,6 +590,7 @@ int32_t bm_server_create(const bm_server_options* opt, bm_server** out) {
         cudaMemset(s->d_claimed, 0, 2 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->work_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->excl_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->worker_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost((void**)&s->h_excl_ctl, sizeof(bmd::Ctl) * kExclSlots) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
@@ -737,6 +749,7 @@ int32_t bm_server_destroy(bm_server* s) {
     }
     if (s->head) __atomic_store_n(&s->head->stop, 1, __ATOMIC_RELEASE);
     if (s->work_stream) cudaStreamSynchronize(s->work_stream);
+    if (s->excl_stream) cudaStreamSynchronize(s->excl_stream);
     if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
     for (auto& kv : s->reqs)
         if (kv.second.uploaded) cudaEventDestroy(kv.second.uploaded);
@@ -745,6 +758,7 @@ int32_t bm_server_destroy(bm_server* s) {
         if (s->excl_ev[k]) cudaEventDestroy(s->excl_ev[k]);
     if (s->h_excl_ctl) cudaFreeHost(s->h_excl_ctl);
     if (s->work_stream) cudaStreamDestroy(s->work_stream);
+    if (s->excl_stream) cudaStreamDestroy(s->excl_stream);
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
     if (s->d_claimed) cudaFree(s->d_claimed);
     if (s->mapped) cudaFreeHost(s->mapped);

@@ -1285,7 +1285,7 @@ ExclusiveDevice g_excl_dev[kMaxDevices];
 std::mutex g_excl_mutex;
 }  // namespace
 
-int32_t bmi::enqueue_match(bmd::Params p, long long nnz, bool wr, int greedy, cudaStream_t st) {
+int32_t bmi::enqueue_match(bmd::Params p, long long nnz, bool wr, int greedy, cudaStream_t st, int blocks_per_sm) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { (void)cudaGetLastError(); return BM_ERR_CUDA; }
     if (dev < 0 || dev >= kMaxDevices) return BM_ERR_UNSUPPORTED;
@@ -1355,8 +1355,10 @@ int32_t bmi::enqueue_match(bmd::Params p, long long nnz, bool wr, int greedy, cu
     if (p.wait_ns <= 0) p.wait_ns = 5000000000LL;
     if (p.total_ns <= 0) p.total_ns = 120000000000LL;
     void* args[] = {&p};
-    const cudaError_t e = wr ? cudaLaunchCooperativeKernel((const void*)k_match<true, true>, d.grid[1], B, args, 0, st)
-                             : cudaLaunchCooperativeKernel((const void*)k_match<false, true>, d.grid[0], B, args, 0, st);
+    int grid = d.grid[wr ? 1 : 0];
+    if (blocks_per_sm > 0 && grid > blocks_per_sm * d.sms) grid = blocks_per_sm * d.sms;
+    const cudaError_t e = wr ? cudaLaunchCooperativeKernel((const void*)k_match<true, true>, grid, B, args, 0, st)
+                             : cudaLaunchCooperativeKernel((const void*)k_match<false, true>, grid, B, args, 0, st);
     if (e != cudaSuccess) { (void)cudaGetLastError(); return BM_ERR_CUDA; }
     return BM_OK;
 }

@@ -165,8 +165,9 @@ def test_idle_workers_leave_and_come_back():
 
 
 def test_large_requests_run_alone_on_the_whole_gpu():
-    """Requests with at least exclusive_min_edges edges run alone on the whole
-    GPU (the single-graph persistent kernel) while the others run on worker
+    """Requests with at least exclusive_min_edges edges run on the single-graph
+    persistent kernel -- alone on the whole GPU, or beside the workers on one
+    block per SM each (exclusive_alongside) -- while the others run on worker
     blocks; mixed in one stream, every result is exact and valid.  A malformed
     large request is reported as such and the requests behind it still run.
     With the threshold at 0 every request stays on the workers."""
@@ -176,8 +177,9 @@ def test_large_requests_run_alone_on_the_whole_gpu():
     assert any(big) and not all(big)
     bad_ri = reqs[0].row_idx.copy()
     bad_ri[len(bad_ri) // 2] = reqs[0].n_rows  # one row id out of range
-    for threshold, expect_alone in ((20000, sum(big) * 2), (0, 0)):
-        with bmatch.Server(keep_results=1, pool_bytes=1 << 30, exclusive_min_edges=threshold) as srv:
+    for threshold, alongside, expect_alone in ((20000, 0, sum(big) * 2), (20000, 1, sum(big) * 2), (0, 0, 0)):
+        with bmatch.Server(keep_results=1, pool_bytes=1 << 30, exclusive_min_edges=threshold,
+                           exclusive_alongside=alongside) as srv:
             ids = [srv.submit(g.n_rows, g.n_cols, g.col_ptr, g.row_idx) for g in reqs]
             rid_bad = srv.submit(reqs[0].n_rows, reqs[0].n_cols, reqs[0].col_ptr, bad_ri)
             ids += [srv.submit(g.n_rows, g.n_cols, g.col_ptr, g.row_idx) for g in reqs]
