@@ -439,7 +439,7 @@ def bench_batched(args, torch, bmatch, stream, flush):
     return {
         "workload": BATCH_WORKLOAD.replace("4,096", f"{G_all:,}", 1), "graphs": G, "rows": R, "cols": C, "edges": E,
         "generate_s": round(t_gen, 2),
-        "ms": batch_ms, "graphs_per_s": G / (batch_ms * 1e-3),
+        "ms": batch_ms, "ms_all": [round(t, 3) for t in times], "graphs_per_s": G / (batch_ms * 1e-3),
         "gteps": E / (batch_ms * 1e-3) / 1e9,
         "one_by_one_ms": one_ms, "one_by_one_graphs_per_s": G / (one_ms * 1e-3),
         "speedup_vs_one_by_one": one_ms / batch_ms,
