@@ -350,7 +350,11 @@ typedef struct bm_server_options {
                                     their own stream beside the workers (one block per SM each,
                                     so both stay resident and small requests do not wait behind
                                     large ones); 0: the workers leave first and the request has
-                                    the whole GPU                                              */
+                                    the whole GPU.  Sharing assumes no other kernel holds the
+                                    SMs' second block slot meanwhile (another server on the same
+                                    GPU, say); if one does, the large request's grid waits for
+                                    it, and a wait past wait limits fails the request with
+                                    BM_ERR_TIMEOUT                                             */
     int64_t exclusive_min_edges; /* requests with at least this many edges run on the single-graph
                                     persistent kernel (one after another; beside the workers or
                                     alone, see exclusive_alongside) instead of on one worker
