@@ -588,7 +588,7 @@ def bench_serving(args, torch, bmatch):
     return {"workload": SERVE_WORKLOAD, "distinct_request_graphs": len(host),
             "requests_per_run": N, "mean_edges_per_request": mean_edges, "generate_s": round(t_gen, 1),
             "lambda_max_rps": lam, "runs": runs, "worker_grid": st["grid"], "worker_block": st["block"],
-            "exclusive_min_edges": int(srv_opts_threshold), "requests_run_alone": int(st["exclusive_runs"]),
+            "exclusive_min_edges": int(srv_opts_threshold), "requests_on_single_graph_kernel": int(st["exclusive_runs"]),
             "exclusive_alongside": int(srv_alongside),
             "one_by_one": one, "one_by_one_rps": one["rps"],
             "speedup_vs_one_by_one": lam / one["rps"] if one["rps"] else None,

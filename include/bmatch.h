@@ -358,7 +358,7 @@ typedef struct bm_server_options {
     int64_t exclusive_min_edges; /* requests with at least this many edges run on the single-graph
                                     persistent kernel (one after another; beside the workers or
                                     alone, see exclusive_alongside) instead of on one worker
-                                    block; 0 = never (default 262,144)                        */
+                                    block; 0 = never (default 524,288)                        */
     int64_t reserved[3];
 } bm_server_options;
 

@@ -532,7 +532,7 @@ void bm_server_default_options(bm_server_options* o) {
     o->keep_results = 0;
     o->idle_timeout_ns = 50000000;  // 50 ms
     o->poll_interval_us = 5;
-    o->exclusive_min_edges = 1 << 18;
+    o->exclusive_min_edges = 1 << 19;
     o->exclusive_alongside = 1;
 }
 
