@@ -5,8 +5,9 @@ leg import this package.  It shares no code with the CUDA path.
 
 * ``bm_oracle.c`` (compiled here with the host C compiler, loaded by ctypes):
   greedy initial matching, Hopcroft-Karp, matching validation, the Koenig
-  certificate and the alternating-BFS levels -- see that file's header for the
-  passages of arXiv 1303.1379 each one follows.
+  certificate, the alternating-BFS levels and the method itself run level by
+  level with fixed tie-break rules -- see that file's header for the passages
+  of arXiv 1303.1379 each one follows.
 * pure Python, for tiny graphs only: exhaustive search over edge subsets and a
   dynamic program over row bitmasks, both straight from the definition of a
   maximum matching (Section 2).
@@ -74,6 +75,8 @@ def _load():
             lib.orc_hk_batch.argtypes = [ctypes.c_int32, I32P, I32P, I64P, I64P, I64P, I32P, I32P,
                                          I32P, I32P, ctypes.c_int32, I64P]
             lib.orc_hk_batch.restype = ctypes.c_int
+            lib.orc_apfb_wr_det.argtypes = g6 + [ctypes.c_int32, I64P]
+            lib.orc_apfb_wr_det.restype = ctypes.c_int64
             lib.orc_num_threads.argtypes = []
             lib.orc_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -166,6 +169,28 @@ def hk_batch(batch, greedy_first=True):
     if rc != 0:
         raise ValueError("hk_batch failed")
     return rm, cm, card
+
+
+DET_STATS = ("phases", "levels", "endpoints", "inserted", "columns_expanded", "edges_scanned",
+             "edges_to_matched", "alternate_steps", "roots")
+
+
+def apfb_wr_det(n_rows, n_cols, col_ptr, row_idx, rmatch=None, cmatch=None, apsb=False):
+    """The method (Algorithm 1 with GPUBFS-WR, one endpoint per root, and
+    Alternate) run level by level with the smallest-id tie-break rules of
+    orc_apfb_wr_det, from an optional valid initial matching.
+    Returns (rmatch, cmatch, |M|, stats dict keyed by DET_STATS)."""
+    cp, ri = _i32(col_ptr), _i32(row_idx)
+    if rmatch is None:
+        rm, cm = empty_matching(n_rows, n_cols)
+    else:
+        rm, cm = _i32(rmatch).copy(), _i32(cmatch).copy()
+    st = np.zeros(len(DET_STATS), np.int64)
+    card = _load().orc_apfb_wr_det(n_rows, n_cols, _p(cp), _p(ri), _p(rm), _p(cm), int(bool(apsb)),
+                                   _p(st, I64P))
+    if card < 0:
+        raise MemoryError("apfb_wr_det")
+    return rm, cm, int(card), dict(zip(DET_STATS, (int(x) for x in st)))
 
 
 def num_threads() -> int:

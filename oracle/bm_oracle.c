@@ -35,6 +35,13 @@
  *                       of Algorithm 1) assigns to bfs_array, offset by L0 --
  *                       and the set of free rows that the BFS reaches.
  *   orc_hk_batch        orc_hopcroft_karp over many graphs of a batch.
+ *   orc_apfb_wr_det     the method itself -- Algorithm 1 (APFB, or APsB)
+ *                       with GPUBFS-WR (Algorithm 4) keeping one endpoint per
+ *                       root (the -(row) refinement of Section 3) and
+ *                       Alternate (Algorithm 3) -- run one level at a time,
+ *                       with each choice that the parallel version leaves to
+ *                       whichever thread comes first fixed by a smallest-id
+ *                       rule (the rules are listed at the function).
  *
  * All indices are int32 and the arithmetic is exact integer.
  */
@@ -296,6 +303,169 @@ ORC_EXPORT int orc_hk_batch(int32_t n_graphs, const int32_t *nr, const int32_t *
         card_out[k] = card;
     }
     return bad ? ORC_BAD_ARG : ORC_OK;
+}
+
+/* The method of Sections 2-3 on one graph, one BFS level at a time, every
+ * choice that the parallel method leaves to a race fixed by a rule:
+ *   - Roots (Algorithm 1, InitBfsArray): the unmatched columns that have at
+ *     least one row; each starts its own tree at level L0.
+ *   - Level L (Algorithm 4 loop body): a column whose root already owns an
+ *     endpoint is skipped (the GPUBFS-WR early exit); any other column scans
+ *     its rows.  A matched row leads to its column; if that column is not yet
+ *     in a tree it joins level L + 1, and of all level-L columns that reach it
+ *     the smallest id becomes its predecessor (and gives it its root).  An
+ *     unmatched row that no root owns yet offers itself to the smallest
+ *     (root, column) pair that reaches it at this level.
+ *   - End of level L: every root that received offers takes the smallest
+ *     offering row as its one endpoint (the -(row) refinement); the other
+ *     offering rows stay unmatched and may be reached again later.  A root
+ *     that took an endpoint at level L stops from level L + 1 on; the columns
+ *     it claimed for level L + 1 stay claimed.
+ *   - The search ends after a level that claims no column (APFB), or after
+ *     the first level that yields an endpoint (APsB, apsb != 0).
+ *   - Alternate (Algorithm 3): every endpoint's path is walked back to its
+ *     root, each column taking the row below it; the trees are disjoint, so
+ *     the walks never meet.
+ *   - Algorithm 1's outer loop stops after a search without endpoints, or
+ *     when no root is left.
+ * rmatch/cmatch: a valid initial matching in, the maximum matching out.
+ * stats (nullable, 9 entries): phases (outer iterations, the final empty one
+ * included), BFS levels, endpoints, columns inserted into a level, columns
+ * expanded, edges scanned, scanned edges whose row was matched, Alternate
+ * steps (columns rematched), roots over all searches.
+ * Returns |M| or a negative error code. */
+ORC_EXPORT int64_t orc_apfb_wr_det(int32_t nr, int32_t nc, const int32_t *cp, const int32_t *ri,
+                                   int32_t *rmatch, int32_t *cmatch, int32_t apsb,
+                                   int64_t *stats) {
+    const int32_t L0 = 2;
+    const size_t NC = (size_t)(nc ? nc : 1), NR = (size_t)(nr ? nr : 1);
+    int32_t *clev = malloc(sizeof(int32_t) * NC);    /* level at which the column joined a tree, -1 none */
+    int32_t *par = malloc(sizeof(int32_t) * NC);     /* predecessor column, -1 for a root */
+    int32_t *croot = malloc(sizeof(int32_t) * NC);   /* root of the column's tree */
+    int32_t *served = malloc(sizeof(int32_t) * NC);  /* per root: its endpoint row, -1 none */
+    int32_t *pick = malloc(sizeof(int32_t) * NC);    /* per root: smallest offering row this level */
+    int32_t *front = malloc(sizeof(int32_t) * NC);
+    int32_t *next = malloc(sizeof(int32_t) * NC);
+    int32_t *off_root = malloc(sizeof(int32_t) * NR);  /* offer of an unmatched row, -1 none */
+    int32_t *off_col = malloc(sizeof(int32_t) * NR);
+    int32_t *offered = malloc(sizeof(int32_t) * NR);   /* rows with an offer this level */
+    uint8_t *owned = malloc(NR);                        /* row is some root's endpoint this search */
+    int32_t *eps = malloc(sizeof(int32_t) * NR);
+    int32_t *epar = malloc(sizeof(int32_t) * NR);      /* predecessor column of an endpoint */
+    int64_t rc = 0;
+    if (!clev || !par || !croot || !served || !pick || !front || !next || !off_root || !off_col ||
+        !offered || !owned || !eps || !epar) {
+        rc = ORC_NOMEM;
+        goto done;
+    }
+    int64_t st[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t searches = 0;
+    int no_roots = 0;
+    for (int32_t r = 0; r < nr; ++r) off_root[r] = -1;
+    for (int32_t c = 0; c < nc; ++c) pick[c] = INT32_MAX;
+    for (;;) {
+        int32_t nf = 0;
+        for (int32_t c = 0; c < nc; ++c) {
+            clev[c] = -1;
+            served[c] = -1;
+            if (cmatch[c] == -1 && cp[c + 1] > cp[c]) {
+                clev[c] = L0;
+                par[c] = -1;
+                croot[c] = c;
+                front[nf++] = c;
+            }
+        }
+        if (nf == 0) { no_roots = 1; break; }
+        ++searches;
+        st[8] += nf;
+        memset(owned, 0, NR);
+        int32_t nep = 0;
+        for (int32_t L = L0;; ++L) {
+            ++st[1];
+            int32_t nn = 0, noff = 0;
+            for (int32_t i = 0; i < nf; ++i) {
+                const int32_t c = front[i];
+                const int32_t rho = croot[c];
+                if (served[rho] != -1) continue;
+                ++st[4];
+                for (int32_t e = cp[c]; e < cp[c + 1]; ++e) {
+                    const int32_t r = ri[e];
+                    const int32_t m = rmatch[r];
+                    ++st[5];
+                    if (m >= 0) {
+                        ++st[6];
+                        if (clev[m] == -1) {
+                            clev[m] = L + 1;
+                            par[m] = c;
+                            next[nn++] = m;
+                        } else if (clev[m] == L + 1 && c < par[m]) {
+                            par[m] = c;
+                        }
+                    } else if (!owned[r]) {
+                        if (off_root[r] == -1) {
+                            off_root[r] = rho;
+                            off_col[r] = c;
+                            offered[noff++] = r;
+                        } else if (rho < off_root[r] || (rho == off_root[r] && c < off_col[r])) {
+                            off_root[r] = rho;
+                            off_col[r] = c;
+                        }
+                    }
+                }
+            }
+            for (int32_t i = 0; i < noff; ++i) {
+                const int32_t r = offered[i];
+                if (r < pick[off_root[r]]) pick[off_root[r]] = r;
+            }
+            int found = 0;
+            for (int32_t i = 0; i < noff; ++i) {
+                const int32_t r = offered[i];
+                const int32_t rho = off_root[r];
+                if (pick[rho] == r) {
+                    owned[r] = 1;
+                    served[rho] = r;
+                    epar[r] = off_col[r];
+                    eps[nep++] = r;
+                    found = 1;
+                }
+            }
+            for (int32_t i = 0; i < noff; ++i) {
+                const int32_t r = offered[i];
+                pick[off_root[r]] = INT32_MAX;
+                off_root[r] = -1;
+            }
+            for (int32_t i = 0; i < nn; ++i) croot[next[i]] = croot[par[next[i]]];
+            st[3] += nn;
+            if (nn == 0) break;
+            if (apsb && found) break;
+            int32_t *t = front;
+            front = next;
+            next = t;
+            nf = nn;
+        }
+        st[2] += nep;
+        if (nep == 0) break;
+        for (int32_t i = 0; i < nep; ++i) {
+            int32_t r = eps[i];
+            int32_t c = epar[r];
+            for (;;) {
+                const int32_t below = cmatch[c];
+                cmatch[c] = r;
+                rmatch[r] = c;
+                ++st[7];
+                if (par[c] < 0) break;
+                r = below;
+                c = par[c];
+            }
+        }
+    }
+    st[0] = searches + no_roots;
+    if (stats) memcpy(stats, st, sizeof(st));
+    for (int32_t c = 0; c < nc; ++c) rc += (cmatch[c] >= 0);
+done:
+    free(clev); free(par); free(croot); free(served); free(pick); free(front); free(next);
+    free(off_root); free(off_col); free(offered); free(owned); free(eps); free(epar);
+    return rc;
 }
 
 ORC_EXPORT int orc_num_threads(void) {
