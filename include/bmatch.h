@@ -91,7 +91,21 @@ typedef struct bm_options {
                               > 0 = stop after that many phases with BM_INCOMPLETE          */
     int32_t block_size;    /* threads per block, 0 = default (512); multiple of 32, <= 1024 */
     int32_t blocks_per_sm; /* 0 = as many as fit (capped at 2 x 1024 threads per SM)        */
-    int32_t reserved0;
+    int32_t deterministic; /* 1 = every choice the parallel search leaves to whichever thread
+                              comes first is fixed by a smallest-id rule, one BFS level at a
+                              time (Algorithm 4 read level-synchronously): a column reached
+                              from several columns of a level takes the smallest as its
+                              parent and root; an unmatched row reached by several roots
+                              offers itself to the smallest (root, column); a root takes the
+                              smallest row offered to it as its one endpoint, the other rows
+                              stay unmatched; a root served at level L stops at level L+1.
+                              bm_match, bm_match_from and bm_bfs then return the same
+                              matching and counters on every run and for every block size
+                              (bm_greedy stays racy: install a fixed start for a fixed
+                              result).  Needs the persistent driver, GPUBFS-WR and
+                              wr_one_endpoint = 1 (BM_ERR_INVALID_ARG otherwise); the
+                              context allocates 8*n_cols + 12*n_rows bytes on its first
+                              deterministic call (BM_ERR_NOMEM if that fails).  0 = default */
     int64_t wait_timeout_ns;  /* limit of one device-side barrier wait; 0 = 5 s             */
     int64_t total_timeout_ns; /* limit of one match launch; 0 = 120 s                       */
     int64_t reserved[6];

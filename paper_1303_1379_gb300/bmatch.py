@@ -94,7 +94,7 @@ class bm_options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("bfs", ctypes.c_int32), ("driver", ctypes.c_int32),
                 ("wr_one_endpoint", ctypes.c_int32), ("max_phases", ctypes.c_int32),
                 ("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("wait_timeout_ns", ctypes.c_int64),
+                ("deterministic", ctypes.c_int32), ("wait_timeout_ns", ctypes.c_int64),
                 ("total_timeout_ns", ctypes.c_int64), ("reserved", ctypes.c_int64 * 6)]
 
 

@@ -76,7 +76,8 @@ struct alignas(128) Ctl {
     int32_t phases;            // outer iterations of Algorithm 1, the last (empty) one included
     int32_t n_endpoints_last;  // endpoints of the last BFS (inspection)
     int32_t searches;          // breadth-first searches run (entries of the phase profile)
-    int32_t pad1[10];
+    int32_t dcnt[3];           // deterministic option: rows listed in ecand during a step
+    int32_t pad1[7];
     long long levels;
     long long max_levels;
     long long cols_expanded;
@@ -116,6 +117,12 @@ struct Params {
     long long total_ns;  // limit of the whole launch
     int32_t stamp_base;  // rvis stamp of phase k is stamp_base + k (k >= 1); above every stamp in rvis
     int32_t* chk;        // range-checked build: error word set when an index is out of range (nullable)
+    // deterministic option (nullable otherwise): per column the tree-entry key
+    // (level << 32 | parent), per row the offer key (root << 32 | column), and
+    // the rows that received an offer during the current level
+    unsigned long long* dkey;
+    unsigned long long* ekey;
+    int32_t* ecand;
 };
 
 // Per-block shared state of the steps.
@@ -367,7 +374,9 @@ __device__ __forceinline__ void step_init(const Params& p, int2* q, int slot, Co
 // touched by the search keep their InitBfsArray values): the columns the
 // search inserted go back to "unvisited" and the roots that are still
 // unmatched are appended to the other queue buffer as the next phase's roots.
-template <bool WR>
+// DET (deterministic option): the inserted columns' tree-entry keys and the
+// roots' endpoint picks (the roots' own key words) go back to "none" too.
+template <bool WR, bool DET = false>
 __device__ __forceinline__ void step_next_roots(const Params& p, const int2* q, int n_roots, int tail,
                                                 int2* q_next, int slot, Smem& sm) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -382,6 +391,7 @@ __device__ __forceinline__ void step_next_roots(const Params& p, const int2* q, 
             if (c[u] < 0 || !idx_ok(p, c[u], p.nc)) continue;
             __stcg(&p.level[c[u]], L0 - 1);
             if (WR) __stcg(&p.root[c[u]], -1);
+            if (DET) __stcg(&p.dkey[c[u]], ~0ull);
         }
     }
     const int T = blockDim.x;
@@ -398,6 +408,7 @@ __device__ __forceinline__ void step_next_roots(const Params& p, const int2* q, 
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (c[u] < 0) continue;
+            if (DET) __stcg(&p.dkey[c[u]], ~0ull);
             if (m[u] < 0) {
                 push_block(p, q_next, sm, 0, slot, make_int2(c[u], c[u]));
             } else {
@@ -658,6 +669,207 @@ __device__ __forceinline__ void step_expand(const Params& p, int2* queue, int qb
                                                                                 q <= RV_MAX_Q);
         flush_block(p, queue, sm, qe, slot);
         tile = next_tile;
+    }
+}
+
+// ------------------------------------------------------------------ deterministic option
+// The level step with every choice that the code above leaves to whichever
+// thread comes first fixed by a smallest-id rule, one level at a time (the
+// level-synchronous reading of Algorithm 4 with one endpoint per root):
+//  * Tree entry: dkey[c] holds (level << 32 | parent) once column c is in a
+//    tree, all ones before.  A level-L column that reaches c through c's
+//    matched row takes atomicMin((L + 1) << 32 | itself): an entry from an
+//    earlier level is never replaced, and of the level-L parents the smallest
+//    wins.  The claimer that found the word empty appends c; when the next
+//    level loads c it reads the winner and fills in c's root (the parent's),
+//    level, pred and crec.
+//  * Endpoints: an unmatched row that no root owns keeps, in ekey[r], the
+//    smallest (root << 32 | column) that reaches it during the level; its
+//    first offerer lists it in ecand.  After the level's barrier every listed
+//    row offers itself to its root (atomicMin of the row id in the root's own
+//    dkey word: roots are unmatched, so no claim ever touches it); after one
+//    more barrier each root takes the smallest row that offered itself
+//    (rmatch[r] = -2, pred[r] = the column, level[root] = -(row)); the other
+//    rows stay unmatched and their offers are cleared.
+//  * A root that took an endpoint at level L stops at level L + 1; the
+//    columns it claimed for level L + 1 stay claimed.
+// The matching and every counter are then the same for every run and launch
+// geometry.
+constexpr unsigned long long DKEY_NONE = ~0ull;
+
+// tile_load for the deterministic option: entries of levels after L0 carry
+// no root yet (-1); each is completed here from its tree-entry word before
+// the GPUBFS-WR root test.  Ends with __syncthreads.
+template <bool NC = true>
+__device__ __forceinline__ void tile_load_det(const Params& p, const int2* queue, int qb, int q, int first, int tw,
+                                              int lvl, Smem& sm, Counters& cnt, int32_t* tile_ctr, int grab = 1,
+                                              int ctr_base = -1) {
+    const int t = threadIdx.x;
+    const int i = first + t;
+    int c = -1, beg = 0, deg = 0, myroot = -1, rlev = L0;
+    if (t < tw && i < q) {
+        const int2 ent = __ldcg(&queue[qb + i]);
+        c = ent.x;
+        if (!idx_ok(p, c, p.nc)) {  // checked build only
+            c = -1;
+        } else {
+            beg = ld_csr<NC>(&p.col_ptr[c]);
+            deg = ld_csr<NC>(&p.col_ptr[c + 1]) - beg;
+            if (lvl == L0) {
+                myroot = ent.y;  // a root: (c, c)
+            } else {
+                const unsigned long long k = __ldcg(&p.dkey[c]);
+                const int par = (int)(unsigned)(k & 0xffffffffull);
+                const int row = __ldcg(&p.cmatch[c]);
+                if (!idx_ok(p, par, p.nc) || !idx_ok(p, row, p.nr)) {
+                    c = -1;
+                } else {
+                    myroot = __ldcg(&p.root[par]);
+                    __stcg(&p.root[c], myroot);
+                    __stcg(&p.level[c], lvl);
+                    __stcg(&p.pred[row], par);
+                    __stcg(&p.crec[c], make_int2(par, row));
+                }
+            }
+            if (c >= 0 && !idx_ok(p, myroot, p.nc)) c = -1;
+            if (c >= 0) rlev = __ldcg(&p.level[myroot]);
+        }
+    }
+    if (t == 0 && tile_ctr) sm.tile = (ctr_base < 0 ? (int)gridDim.x : ctr_base) + atomicAdd(tile_ctr, grab);
+    const int off = block_exclusive_scan(c >= 0 ? deg : 0, sm);
+    if (rlev < L0 - 1) c = -1;  // Algorithm 4: root already served
+    if (c >= 0) cnt.cols++;
+    sm.off[t] = off;
+    sm.beg[t] = beg;
+    sm.col[t] = c;
+    sm.root[t] = myroot;
+    __syncthreads();
+}
+
+// tile_edges for the deterministic option (the rules above); lvl is the level
+// of the tile's columns, slot the step's counter slot (ecand count).
+template <class PushCol, bool NC = true>
+__device__ __forceinline__ void tile_edges_det(const Params& p, int tw, int lvl, int slot, Smem& sm, Counters& cnt,
+                                               PushCol push_col) {
+    const int T = blockDim.x;
+    const int t = threadIdx.x;
+    const int total = sm.total;
+    const unsigned long long next_lv = (unsigned long long)(unsigned)(lvl + 1) << 32;
+    for (int e0 = 0; e0 < total; e0 += T * ILP) {
+        int own[ILP], r[ILP], cm[ILP];
+        unsigned long long key[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            const int e = e0 + u * T + t;
+            own[u] = -1;
+            r[u] = -1;
+            if (e < total) {
+                int lo = 0, hi = tw - 1;  // last k with off[k] <= e
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (sm.off[mid] <= e) lo = mid; else hi = mid - 1;
+                }
+                if (sm.col[lo] >= 0) {
+                    own[u] = lo;
+                    r[u] = ld_csr<NC>(&p.row_idx[sm.beg[lo] + (e - sm.off[lo])]);
+                    if (!idx_ok(p, r[u], p.nr)) own[u] = r[u] = -1;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) cm[u] = own[u] >= 0 ? __ldcg(&p.rmatch[r[u]]) : -3;
+#pragma unroll
+        for (int u = 0; u < ILP; ++u)
+            if (cm[u] >= 0 && !idx_ok(p, cm[u], p.nc)) cm[u] = -3;  // checked build only
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) key[u] = cm[u] >= 0 ? __ldcg(&p.dkey[cm[u]]) : 0ull;
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            if (own[u] < 0) continue;
+            const int col = sm.col[own[u]];
+            cnt.edges++;
+            if (cm[u] >= 0) {
+                cnt.em++;
+                // keys only decrease: a stale key that is not above ours is final
+                const unsigned long long want = next_lv | (unsigned)col;
+                if (key[u] > want && atomicMin(&p.dkey[cm[u]], want) == DKEY_NONE) push_col(make_int2(cm[u], -1));
+            } else if (cm[u] == -1) {
+                const unsigned long long want =
+                    ((unsigned long long)(unsigned)sm.root[own[u]] << 32) | (unsigned)col;
+                if (atomicMin(&p.ekey[r[u]], want) == DKEY_NONE) push(p.ecand, 0, &p.ctl->dcnt[slot], r[u]);
+                sm.has_ep = 1;
+            }
+        }
+    }
+}
+
+// step_expand for the deterministic option (same schedule: guided ranges on
+// wide levels, one static tile per block on narrow ones).
+__device__ __forceinline__ void step_expand_det(const Params& p, int2* queue, int qb, int qe, int lvl, int slot,
+                                                Counters& cnt, Smem& sm) {
+    const int q = qe - qb;
+    int tw = (q + gridDim.x - 1) / gridDim.x;
+    tw = (tw + 31) & ~31;
+    if (tw > (int)blockDim.x) tw = blockDim.x;
+    if (tw < 32) tw = 32;
+    const int ntiles = (q + tw - 1) / tw;
+    const bool narrow = ntiles <= (int)gridDim.x;
+    auto push_col = [&](int2 v) { push_block(p, queue, sm, qe, slot, v); };
+    if (!narrow) {
+        const int G = gridDim.x, T = blockDim.x;
+        auto clamp_w = [&](long long w) { return (int)min((long long)T, max(32LL, (w + 31) & ~31LL)); };
+        const int w0 = clamp_w(((long long)q + 2 * G - 1) / (2 * G));
+        int first = (int)min((long long)blockIdx.x * w0, (long long)q);
+        int width = w0;
+        while (first < q) {  // block-uniform
+            const int grab = clamp_w(((long long)q - first - width) / (2 * G));
+            tile_load_det(p, queue, qb, q, first, width, lvl, sm, cnt, &p.ctl->tcnt[slot], grab, G * w0);
+            const int next_first = sm.tile;
+            tile_edges_det(p, width, lvl, slot, sm, cnt, push_col);
+            flush_block(p, queue, sm, qe, slot);
+            first = next_first;
+            width = grab;
+        }
+        return;
+    }
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {  // block-uniform
+        tile_load_det(p, queue, qb, q, tile * tw, tw, lvl, sm, cnt, nullptr);
+        tile_edges_det(p, tw, lvl, slot, sm, cnt, push_col);
+        flush_block(p, queue, sm, qe, slot);
+    }
+}
+
+// After a level with offers (n rows listed in ecand): every listed row
+// offers itself to the root that won it.
+__device__ __forceinline__ void step_det_offer(const Params& p, int n) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthr = gridDim.x * blockDim.x;
+    for (int i = tid; i < n; i += nthr) {
+        const int r = __ldcg(&p.ecand[i]);
+        if (!idx_ok(p, r, p.nr)) continue;
+        const int rho = (int)(__ldcg(&p.ekey[r]) >> 32);
+        if (!idx_ok(p, rho, p.nc)) continue;
+        atomicMin(&p.dkey[rho], (unsigned long long)(unsigned)r);
+    }
+}
+
+// Then every root takes the smallest row that offered itself as its one
+// endpoint; every listed row's offer is cleared.
+__device__ __forceinline__ void step_det_take(const Params& p, int n) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthr = gridDim.x * blockDim.x;
+    for (int i = tid; i < n; i += nthr) {
+        const int r = __ldcg(&p.ecand[i]);
+        if (!idx_ok(p, r, p.nr)) continue;
+        const unsigned long long k = __ldcg(&p.ekey[r]);
+        const int rho = (int)(k >> 32);
+        if (idx_ok(p, rho, p.nc) && __ldcg(&p.dkey[rho]) == (unsigned long long)(unsigned)r) {
+            __stcg(&p.rmatch[r], -2);
+            __stcg(&p.pred[r], (int)(unsigned)(k & 0xffffffffull));
+            __stcg(&p.level[rho], -r);
+            push(p.endpoints, 0, &p.ctl->ep_phase, r);
+        }
+        __stcg(&p.ekey[r], DKEY_NONE);
     }
 }
 

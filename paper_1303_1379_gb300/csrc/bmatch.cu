@@ -46,8 +46,11 @@ struct LeaderStats {
 // One launch per match: Algorithm 1 with both loops on the device.  RV: small
 // BFS levels claim columns through the row stamps p.rvis (a context's
 // launches); without it every level claims through the column levels (the
-// allocation-free entry point).
-template <bool WR, bool RV>
+// allocation-free entry point).  DET: the deterministic option (GPUBFS-WR
+// with one endpoint per root; p.dkey, p.ekey and p.ecand set): each level
+// is followed, when it produced offers, by the two passes that hand rows to
+// roots.
+template <bool WR, bool RV, bool DET = false>
 __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
     using namespace bmd;
     Ctl* ctl = p.ctl;
@@ -79,6 +82,7 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
             ctl->ecnt[(s + 1) % 3] = 0;
             ctl->icnt[(s + 1) % 3] = 0;
             ctl->tcnt[(s + 1) % 3] = 0;
+            if (DET) ctl->dcnt[(s + 1) % 3] = 0;
             ctl->ep_phase = 0;
         }
         step_init<WR>(p, qcur, s % 3, cnt, sm);
@@ -101,11 +105,24 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
         if (leader) { ls.levels = 0; ls.first_ep = 0; ls.last_ep = 0; ls.roots_total += n_roots; }
         for (;;) {
             const int s2 = step++;
-            if (leader) { ctl->qcnt[(s2 + 1) % 3] = 0; ctl->ecnt[(s2 + 1) % 3] = 0; ctl->icnt[(s2 + 1) % 3] = 0; ctl->tcnt[(s2 + 1) % 3] = 0; }
-            step_expand<WR, RV, true>(p, qcur, qb, qe, lvl, s2 % 3, cnt, sm, p.stamp_base + phases);
-            if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
+            if (leader) {
+                ctl->qcnt[(s2 + 1) % 3] = 0; ctl->ecnt[(s2 + 1) % 3] = 0; ctl->icnt[(s2 + 1) % 3] = 0; ctl->tcnt[(s2 + 1) % 3] = 0;
+                if (DET) ctl->dcnt[(s2 + 1) % 3] = 0;
+            }
+            if constexpr (DET) step_expand_det(p, qcur, qb, qe, lvl, s2 % 3, cnt, sm);
+            else step_expand<WR, RV, true>(p, qcur, qb, qe, lvl, s2 % 3, cnt, sm, p.stamp_base + phases);
+            if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, DET ? &ctl->dcnt[s2 % 3] : nullptr)) goto out;
             const int nq = sm.bc_a;           // columns inserted at this level
-            const bool found = sm.bc_b > 0;   // some block claimed an endpoint
+            const bool found = sm.bc_b > 0;   // some block claimed an endpoint (DET: received an offer)
+            if constexpr (DET) {
+                if (found) {  // hand the offering rows to their roots
+                    const int n_off = sm.bc_c;
+                    step_det_offer(p, n_off);
+                    if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
+                    step_det_take(p, n_off);
+                    if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
+                }
+            }
             if (leader) {
                 const int lv_now = ++ls.levels;
                 if (found) {
@@ -154,9 +171,10 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
             const int s3 = step++;
             if (leader) {
                 ctl->qcnt[(s3 + 1) % 3] = 0; ctl->ecnt[(s3 + 1) % 3] = 0; ctl->icnt[(s3 + 1) % 3] = 0; ctl->tcnt[(s3 + 1) % 3] = 0;
+                if (DET) ctl->dcnt[(s3 + 1) % 3] = 0;
                 ctl->ep_phase = 0;
             }
-            step_next_roots<WR>(p, qcur, n_roots, tail, qnext, s3 % 3, sm);
+            step_next_roots<WR, DET>(p, qcur, n_roots, tail, qnext, s3 % 3, sm);
             if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
             n_roots = sm.bc_a;
 #ifdef BM_CHECKED
@@ -490,8 +508,13 @@ struct bm_ctx {
     int32_t sticky = 0;
     int device = 0;
     int num_sms = 0;
-    int coop_grid[2] = {0, 0};  // blocks of k_match<false, true>, k_match<true, true>
+    int coop_grid[3] = {0, 0, 0};  // blocks of k_match<false, true>, <true, true>, <true, true, true>
     int block = kDefaultBlock;
+    // deterministic option: allocated on its first use, [dkey nc][ekey nr][ecand nr]
+    void* det_arena = nullptr;
+    unsigned long long* dkey = nullptr;
+    unsigned long long* ekey = nullptr;
+    int32_t* ecand = nullptr;
 };
 
 namespace {
@@ -517,6 +540,10 @@ int32_t check_options(const bm_options& o) {
         return BM_ERR_INVALID_ARG;
     if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 1024 || o.block_size % 32 != 0))
         return BM_ERR_INVALID_ARG;
+    if (o.deterministic != 0 && o.deterministic != 1) return BM_ERR_INVALID_ARG;
+    if (o.deterministic &&
+        (o.driver != BM_DRIVER_PERSISTENT || o.bfs != BM_GPUBFS_WR || o.wr_one_endpoint != 1))
+        return BM_ERR_INVALID_ARG;
     return BM_OK;
 }
 
@@ -529,10 +556,12 @@ int grid_for(bm_ctx* ctx, int n) {  // plain launches: enough blocks to fill the
 
 int32_t configure(bm_ctx* ctx) {
     ctx->block = ctx->opt.block_size ? ctx->opt.block_size : kDefaultBlock;
-    for (int wr = 0; wr < 2; ++wr) {
+    for (int wr = 0; wr < 3; ++wr) {
         int per_sm = 0;
-        cudaError_t e = wr ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true, true>, ctx->block, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<false, true>, ctx->block, 0);
+        cudaError_t e =
+            wr == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true, true, true>, ctx->block, 0)
+            : wr    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true, true>, ctx->block, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<false, true>, ctx->block, 0);
         if (e != cudaSuccess) return cuda_fail(ctx, e);
         int cap = 2048 / ctx->block;  // at most 2048 resident threads per SM
         if (ctx->opt.blocks_per_sm > 0 && ctx->opt.blocks_per_sm < cap) cap = ctx->opt.blocks_per_sm;
@@ -717,6 +746,31 @@ int32_t run(bm_ctx* ctx, bool bfs_only) {
     p.stamp_base = (int32_t)ctx->stamp_next;
     ctx->stamp_next += span;
     void* args[] = {&p};
+    if (ctx->opt.deterministic) {
+        const size_t nr1 = (size_t)(ctx->nr ? ctx->nr : 1), nc1 = (size_t)(ctx->nc ? ctx->nc : 1);
+        const size_t off_ek = (8 * nc1 + 255) & ~size_t(255);
+        const size_t off_ec = off_ek + ((8 * nr1 + 255) & ~size_t(255));
+        if (!ctx->det_arena) {
+            if (cudaMalloc(&ctx->det_arena, off_ec + 4 * nr1) != cudaSuccess) {
+                (void)cudaGetLastError();
+                ctx->det_arena = nullptr;
+                return BM_ERR_NOMEM;
+            }
+            char* a = (char*)ctx->det_arena;
+            ctx->dkey = (unsigned long long*)a;
+            ctx->ekey = (unsigned long long*)(a + off_ek);
+            ctx->ecand = (int32_t*)(a + off_ec);
+        }
+        // every key "none" (all ones) at launch; the kernel restores that between phases
+        BM_CUDA(ctx, cudaMemsetAsync(ctx->det_arena, 0xff, off_ec, ctx->stream));
+        p.dkey = ctx->dkey;
+        p.ekey = ctx->ekey;
+        p.ecand = ctx->ecand;
+        cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_match<true, true, true>, ctx->coop_grid[2],
+                                                    ctx->block, args, 0, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e);
+        return BM_OK;
+    }
     cudaError_t e = wr ? cudaLaunchCooperativeKernel((const void*)k_match<true, true>, ctx->coop_grid[1], ctx->block, args, 0, ctx->stream)
                        : cudaLaunchCooperativeKernel((const void*)k_match<false, true>, ctx->coop_grid[0], ctx->block, args, 0, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
@@ -748,7 +802,7 @@ int32_t finish(bm_ctx* ctx, int32_t* card_out, bm_stats* stats) {
         stats->kernel_ns = h.kernel_ns;
         stats->roots = h.roots;
         if (ctx->opt.driver == BM_DRIVER_PERSISTENT) {
-            stats->grid = ctx->coop_grid[ctx->opt.bfs == BM_GPUBFS_WR ? 1 : 0];
+            stats->grid = ctx->coop_grid[ctx->opt.deterministic ? 2 : ctx->opt.bfs == BM_GPUBFS_WR ? 1 : 0];
             stats->block = ctx->block;
         }
     }
@@ -1127,6 +1181,7 @@ int32_t bm_destroy(bm_ctx* ctx) {
     if (!ctx) return BM_ERR_INVALID_ARG;
     if (ctx->stream || ctx->arena) cudaStreamSynchronize(ctx->stream);
     if (ctx->arena) cudaFree(ctx->arena);
+    if (ctx->det_arena) cudaFree(ctx->det_arena);
     if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
     (void)cudaGetLastError();
     delete ctx;

@@ -94,3 +94,18 @@ def test_binding_rejects_bad_buffers():
         bmatch._ptr(torch.zeros(4, dtype=torch.int64))
     with pytest.raises(TypeError):
         bmatch._ptr(torch.zeros(8, dtype=torch.int32)[::2])
+
+
+def test_deterministic_option_is_checked_before_any_device_call():
+    # bm_create checks its options first: an invalid deterministic setting
+    # (a value other than 0/1, or a variant the option does not cover) is
+    # refused with BM_ERR_INVALID_ARG without touching a GPU.
+    lib = bmatch.load()
+    ctx = ctypes.c_void_p()
+    bad = [dict(deterministic=2), dict(deterministic=1, driver=1), dict(deterministic=1, bfs=0),
+           dict(deterministic=1, wr_one_endpoint=0)]
+    for kw in bad:
+        o = bmatch.default_options(**kw)
+        rc = lib.bm_create(10, 10, 0, None, None, None, ctypes.byref(o), ctypes.byref(ctx))
+        assert rc == bmatch.BM_ERR_INVALID_ARG, kw
+        assert not ctx.value

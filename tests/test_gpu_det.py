@@ -1,0 +1,129 @@
+"""The deterministic option on the GPU: element-by-element parity with the
+oracle's level-by-level run of the method under the same smallest-id rules
+(orc_apfb_wr_det), and the same result for every run and launch geometry.
+
+With the option on, every choice the parallel search leaves to a race is a
+minimum over a set that one BFS level fixes, so the CUDA path must return
+exactly the oracle's rmatch and cmatch -- not just its |M| -- and exactly its
+counters (phases, levels, endpoints, inserted and expanded columns, scanned
+edges, Alternate steps, roots).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1303_1379_gb300 import synth
+
+from helpers import assert_maximum, gpu_match, oracle_max
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+STATS = oracle.DET_STATS
+
+GRAPHS = {
+    "uniform-ragged": lambda: synth.uniform_graph(20_011, 19_993, 6, seed=11),
+    "uniform-tall": lambda: synth.uniform_graph(40_000, 9_001, 3, seed=12),
+    "uniform-wide": lambda: synth.uniform_graph(9_001, 40_000, 3, seed=13),
+    "rmat15": lambda: synth.rmat_graph(15, 1 << 19, seed=3),
+    "rmat17-rcp": lambda: synth.permute_graph(synth.rmat_graph(17, 1 << 21, seed=4), seed=5),
+    "stencil150": lambda: synth.stencil_graph(150, 2_250, 0.05, seed=2),
+}
+_cache = {}
+
+
+def graph(name):
+    if name not in _cache:
+        _cache[name] = GRAPHS[name]()
+    return _cache[name]
+
+
+def start(g, how):
+    if how == "empty":
+        return None
+    rm, cm, _ = oracle.greedy(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+    return rm, cm
+
+
+def check_same_as_oracle(g, init, apsb, **options):
+    rm0, cm0 = (None, None) if init is None else init
+    w_rm, w_cm, w_card, w_st = oracle.apfb_wr_det(g.n_rows, g.n_cols, g.col_ptr, g.row_idx, rm0, cm0,
+                                                  apsb=apsb)
+    rm, cm, card, st = gpu_match(g, init, deterministic=1, mode=1 if apsb else 0, **options)
+    assert card == w_card
+    assert {k: st[k] for k in STATS} == w_st
+    np.testing.assert_array_equal(rm, w_rm)
+    np.testing.assert_array_equal(cm, w_cm)
+    return rm, cm, card, st
+
+
+@pytest.mark.parametrize("apsb", [False, True], ids=["APFB", "APsB"])
+@pytest.mark.parametrize("how", ["empty", "greedy"])
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_same_matching_and_counters_as_the_oracle(name, how, apsb):
+    g = graph(name)
+    rm, cm, card, _ = check_same_as_oracle(g, start(g, how), apsb)
+    assert_maximum(g, rm, cm, card, oracle_max(g))
+
+
+@pytest.mark.parametrize("block", [64, 128, 256, 1024])
+def test_every_block_size_gives_the_same_result(block):
+    # tiles, guided ranges and the number of blocks all change with the block
+    # size; the result must not
+    g = graph("rmat17-rcp")
+    check_same_as_oracle(g, start(g, "greedy"), False, block_size=block)
+    check_same_as_oracle(g, start(g, "greedy"), False, block_size=block, blocks_per_sm=1)
+
+
+def test_repeated_runs_on_one_context_agree():
+    from paper_1303_1379_gb300 import bmatch
+    from helpers import to_dev
+    g = graph("stencil150")
+    rm0, cm0 = start(g, "greedy")
+    cp, ri = to_dev(g)
+    m = bmatch.Matcher(g.n_rows, g.n_cols, g.nnz, cp, ri, deterministic=1)
+    try:
+        outs = []
+        for _ in range(4):
+            m.set_matching(torch.from_numpy(rm0).cuda(), torch.from_numpy(cm0).cuda())
+            rm = torch.empty(g.n_rows, dtype=torch.int32, device="cuda")
+            cm = torch.empty(g.n_cols, dtype=torch.int32, device="cuda")
+            res = m.match(rm, cm)
+            outs.append((rm.cpu().numpy(), cm.cpu().numpy(), {k: res.stats[k] for k in STATS}))
+        for o in outs[1:]:
+            np.testing.assert_array_equal(o[0], outs[0][0])
+            np.testing.assert_array_equal(o[1], outs[0][1])
+            assert o[2] == outs[0][2]
+        # switching the option off and on again on the same context
+        m.set_options(deterministic=0)
+        m.set_matching(torch.from_numpy(rm0).cuda(), torch.from_numpy(cm0).cuda())
+        assert m.match().card == int((outs[0][1] >= 0).sum())
+        m.set_options(deterministic=1)
+        m.set_matching(torch.from_numpy(rm0).cuda(), torch.from_numpy(cm0).cuda())
+        rm = torch.empty(g.n_rows, dtype=torch.int32, device="cuda")
+        m.match(rm)
+        np.testing.assert_array_equal(rm.cpu().numpy(), outs[0][0])
+    finally:
+        m.close()
+
+
+def test_degenerate_graphs():
+    # no edges; one column; a column without rows among others; all matched already
+    cases = [
+        synth.Graph(5, 4, np.zeros(5, np.int32), np.zeros(0, np.int32), "no edges"),
+        synth.Graph(3, 1, np.array([0, 3], np.int32), np.array([0, 1, 2], np.int32), "one column"),
+        synth.Graph(2, 3, np.array([0, 1, 1, 2], np.int32), np.array([1, 1], np.int32), "empty column"),
+    ]
+    for g in cases:
+        rm, cm, card, _ = check_same_as_oracle(g, None, False)
+        assert_maximum(g, rm, cm, card, oracle_max(g))
+    g = graph("uniform-ragged")
+    rm_max, cm_max, _, _ = oracle.hopcroft_karp(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+    check_same_as_oracle(g, (rm_max, cm_max), False)  # maximum already: one empty search
+
+
+@pytest.mark.parametrize("name", ["rmat21", "stencil2000"])
+def test_full_size_workloads_same_as_the_oracle(name):
+    # the benchmark's graphs at full size, from the oracle's greedy start
+    g = synth.workload(name)
+    check_same_as_oracle(g, start(g, "greedy"), False)
