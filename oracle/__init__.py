@@ -75,6 +75,8 @@ def _load():
             lib.orc_hk_batch.argtypes = [ctypes.c_int32, I32P, I32P, I64P, I64P, I64P, I32P, I32P,
                                          I32P, I32P, ctypes.c_int32, I64P]
             lib.orc_hk_batch.restype = ctypes.c_int
+            lib.orc_greedy_rounds.argtypes = g6 + [I64P]
+            lib.orc_greedy_rounds.restype = ctypes.c_int64
             lib.orc_apfb_wr_det.argtypes = g6 + [ctypes.c_int32, I64P]
             lib.orc_apfb_wr_det.restype = ctypes.c_int64
             lib.orc_num_threads.argtypes = []
@@ -169,6 +171,22 @@ def hk_batch(batch, greedy_first=True):
     if rc != 0:
         raise ValueError("hk_batch failed")
     return rm, cm, card
+
+
+def greedy_rounds(n_rows, n_cols, col_ptr, row_idx, rmatch=None, cmatch=None):
+    """Cheap matching by rounds of proposals: each unmatched column proposes
+    to the first unmatched row of its list, each row takes the smallest
+    proposer.  Returns (rmatch, cmatch, |M|, rounds)."""
+    cp, ri = _i32(col_ptr), _i32(row_idx)
+    if rmatch is None:
+        rm, cm = empty_matching(n_rows, n_cols)
+    else:
+        rm, cm = _i32(rmatch).copy(), _i32(cmatch).copy()
+    card = np.zeros(1, np.int64)
+    rounds = _load().orc_greedy_rounds(n_rows, n_cols, _p(cp), _p(ri), _p(rm), _p(cm), _p(card, I64P))
+    if rounds < 0:
+        raise MemoryError("greedy_rounds")
+    return rm, cm, int(card[0]), int(rounds)
 
 
 DET_STATS = ("phases", "levels", "endpoints", "inserted", "columns_expanded", "edges_scanned",

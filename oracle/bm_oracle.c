@@ -35,6 +35,9 @@
  *                       of Algorithm 1) assigns to bfs_array, offset by L0 --
  *                       and the set of free rows that the BFS reaches.
  *   orc_hk_batch        orc_hopcroft_karp over many graphs of a batch.
+ *   orc_greedy_rounds   a cheap matching in rounds of proposals (each row
+ *                       takes its smallest proposer), the start that a
+ *                       parallel machine reproduces exactly.
  *   orc_apfb_wr_det     the method itself -- Algorithm 1 (APFB, or APsB)
  *                       with GPUBFS-WR (Algorithm 4) keeping one endpoint per
  *                       root (the -(row) refinement of Section 3) and
@@ -303,6 +306,52 @@ ORC_EXPORT int orc_hk_batch(int32_t n_graphs, const int32_t *nr, const int32_t *
         card_out[k] = card;
     }
     return bad ? ORC_BAD_ARG : ORC_OK;
+}
+
+/* A cheap matching that a parallel machine computes the same way every time
+ * (the start of the library's deterministic option): in every round, each
+ * unmatched column that still has an unmatched row proposes to the first
+ * unmatched row of its list; every proposed row takes the smallest column
+ * that proposed to it.  Rounds repeat until no column proposes.  The result
+ * is maximal: a column stays unmatched only when all its rows are matched.
+ * rmatch/cmatch in (a valid matching, usually empty) and out; returns the
+ * number of rounds run (the last one without proposals not counted) or a
+ * negative error code; *card_out (nullable) gets |M|. */
+ORC_EXPORT int64_t orc_greedy_rounds(int32_t nr, int32_t nc, const int32_t *cp, const int32_t *ri,
+                                     int32_t *rmatch, int32_t *cmatch, int64_t *card_out) {
+    int32_t *pos = malloc(sizeof(int32_t) * (size_t)(nc ? nc : 1));   /* first row not yet seen matched */
+    int32_t *prop = malloc(sizeof(int32_t) * (size_t)(nr ? nr : 1));  /* smallest proposer this round */
+    int32_t *want = malloc(sizeof(int32_t) * (size_t)(nc ? nc : 1));  /* row proposed to this round, -1 none */
+    if (!pos || !prop || !want) { free(pos); free(prop); free(want); return ORC_NOMEM; }
+    for (int32_t c = 0; c < nc; ++c) pos[c] = cp[c];
+    for (int32_t r = 0; r < nr; ++r) prop[r] = -1;
+    int64_t rounds = 0;
+    for (;;) {
+        int any = 0;
+        for (int32_t c = 0; c < nc; ++c) {
+            want[c] = -1;
+            if (cmatch[c] != -1) continue;
+            while (pos[c] < cp[c + 1] && rmatch[ri[pos[c]]] != -1) ++pos[c];
+            if (pos[c] == cp[c + 1]) continue;
+            const int32_t r = ri[pos[c]];
+            want[c] = r;
+            if (prop[r] == -1 || c < prop[r]) prop[r] = c;
+            any = 1;
+        }
+        if (!any) break;
+        ++rounds;
+        for (int32_t c = 0; c < nc; ++c) {
+            const int32_t r = want[c];
+            if (r >= 0 && prop[r] == c) { rmatch[r] = c; cmatch[c] = r; }
+        }
+        for (int32_t c = 0; c < nc; ++c)
+            if (want[c] >= 0) prop[want[c]] = -1;
+    }
+    int64_t card = 0;
+    for (int32_t c = 0; c < nc; ++c) card += (cmatch[c] >= 0);
+    if (card_out) *card_out = card;
+    free(pos); free(prop); free(want);
+    return rounds;
 }
 
 /* The method of Sections 2-3 on one graph, one BFS level at a time, every

@@ -157,3 +157,53 @@ def test_rules_do_not_depend_on_the_order_of_a_columns_rows():
         other = oracle.apfb_wr_det(nr, nc, g.col_ptr, ri, g_rm, g_cm)
         assert np.array_equal(base[0], other[0]) and np.array_equal(base[1], other[1])
         assert base[2] == other[2] and base[3] == other[3]
+
+
+# ------------------------------------------------------------ cheap matching in rounds
+def test_greedy_rounds_closed_forms():
+    # K_{a,b}: every round all unmatched columns propose to the first free row,
+    # which takes the smallest of them -- column k gets row k in round k + 1.
+    for a, b in [(1, 1), (4, 6), (6, 4), (5, 5)]:
+        cp, ri = csr(b, [list(range(a)) for _ in range(b)])
+        rm, cm, card, rounds = oracle.greedy_rounds(a, b, cp, ri)
+        n = min(a, b)
+        assert card == n and rounds == n
+        assert list(cm[:n]) == list(range(n)) and all(x == -1 for x in cm[n:])
+    # a permutation: first choices never collide, one round
+    perm = [3, 0, 4, 1, 2]
+    cp, ri = csr(5, [[perm[c], (perm[c] + 1) % 5] for c in range(5)])
+    rm, cm, card, rounds = oracle.greedy_rounds(5, 5, cp, ri)
+    assert rounds == 1 and card == 5 and list(cm) == perm
+
+
+def test_greedy_rounds_worked_examples():
+    # Columns 0 and 1 both propose to row 0 first; row 0 takes column 0.
+    # Column 1's other row (1) went to column 2 in the same round, so column
+    # 1 ends unmatched, where the column-order greedy would have matched all.
+    cp, ri = csr(3, [[0], [0, 1], [1, 2]])
+    rm, cm, card, rounds = oracle.greedy_rounds(3, 3, cp, ri)
+    assert (list(rm), list(cm), card, rounds) == ([0, 2, -1], [0, -1, 1], 2, 1)
+    assert oracle.greedy(3, 3, cp, ri)[2] == 3
+    # The loser of round 1 moves on to its next free row in round 2.
+    cp, ri = csr(2, [[0, 1], [0, 2]])
+    rm, cm, card, rounds = oracle.greedy_rounds(3, 2, cp, ri)
+    assert (list(rm), list(cm), card, rounds) == ([0, -1, 1], [0, 2], 2, 2)
+    # A matched column does not propose; its row is not free.
+    rm0 = np.array([-1, -1, 1], np.int32)
+    cm0 = np.array([-1, 2], np.int32)
+    rm, cm, card, rounds = oracle.greedy_rounds(3, 2, cp, ri, rm0, cm0)
+    assert (list(rm), list(cm), card, rounds) == ([0, -1, 1], [0, 2], 2, 1)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_greedy_rounds_is_a_maximal_matching(seed):
+    rng = np.random.default_rng(200 + seed)
+    nr, nc = int(rng.integers(1, 400)), int(rng.integers(1, 400))
+    g = synth.uniform_graph(nr, nc, int(rng.integers(1, 9)), seed=seed)
+    rm, cm, card, rounds = oracle.greedy_rounds(nr, nc, g.col_ptr, g.row_idx)
+    st, c = oracle.validate(nr, nc, g.col_ptr, g.row_idx, rm, cm)
+    assert st == 0 and c == card
+    for col in range(nc):
+        if cm[col] == -1:  # maximal: every row of an unmatched column is matched
+            assert all(rm[r] >= 0 for r in g.row_idx[g.col_ptr[col]:g.col_ptr[col + 1]])
+    assert rounds <= nc
