@@ -56,13 +56,18 @@ struct BatchParams {
     int32_t* pred;
     int2* queue;
     int32_t* endpoints;
+    unsigned long long* dkey;  // deterministic option: per column, per row; rows listed per level
+    unsigned long long* ekey;
+    int32_t* ecand;
     int32_t* card_out;    // [n_graphs]
     int32_t* status_out;  // [n_graphs]
     int32_t* phases_out;  // [n_graphs]
     BatchCtl* ctl;
 };
 
-template <bool WR>
+// DET: the deterministic option (block_match_graph_det; GPUBFS-WR, one
+// endpoint per root, the cheap matching in rounds).
+template <bool WR, bool DET = false>
 __global__ void __launch_bounds__(1024, 1) k_batch(BatchParams bp) {
     __shared__ Smem sm;
     Counters cnt{0, 0, 0, 0, 0};
@@ -91,7 +96,15 @@ __global__ void __launch_bounds__(1024, 1) k_batch(BatchParams bp) {
         p.chk = &bp.ctl->err;
         int card = 0, phases = 0;
         long long levels = 0, eps = 0, ins = 0;
-        const int st = bmd::block_match_graph<WR, true, true>(p, bp.greedy, sm, cnt, card, phases, levels, eps, ins);
+        int st;
+        if constexpr (DET) {
+            p.dkey = bp.dkey + co;
+            p.ekey = bp.ekey + ro;
+            p.ecand = bp.ecand + ro;
+            st = bmd::block_match_graph_det<true>(p, bp.greedy, sm, cnt, card, phases, levels, eps, ins);
+        } else {
+            st = bmd::block_match_graph<WR, true, true>(p, bp.greedy, sm, cnt, card, phases, levels, eps, ins);
+        }
         if (threadIdx.x == 0) {
             bp.card_out[g] = card;
             bp.status_out[g] = st;
@@ -169,6 +182,7 @@ struct bm_batch {
     BatchCtl* h_ctl = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    void* det_arena = nullptr;  // deterministic option, allocated on first use: [dkey cols][ekey rows][ecand rows]
     int32_t* g_rmatch = nullptr;  // matching arrays the captured launch points at
     int32_t* g_cmatch = nullptr;
     int g_greedy = -1;
@@ -211,6 +225,13 @@ BatchParams batch_params(bm_batch* b, int32_t* rmatch, int32_t* cmatch, int gree
     bp.pred = b->pred;
     bp.queue = b->queue;
     bp.endpoints = b->endpoints;
+    if (b->det_arena) {
+        const size_t cols = (size_t)(b->total_cols ? b->total_cols : 1), rows = (size_t)(b->total_rows ? b->total_rows : 1);
+        char* a = (char*)b->det_arena;
+        bp.dkey = (unsigned long long*)a;
+        bp.ekey = (unsigned long long*)(a + ((8 * cols + 255) & ~size_t(255)));
+        bp.ecand = (int32_t*)(a + ((8 * cols + 255) & ~size_t(255)) + ((8 * rows + 255) & ~size_t(255)));
+    }
     bp.card_out = b->card;
     bp.status_out = b->status;
     bp.phases_out = b->phases;
@@ -221,7 +242,9 @@ BatchParams batch_params(bm_batch* b, int32_t* rmatch, int32_t* cmatch, int gree
 int32_t configure_batch(bm_batch* b) {
     b->block = b->opt.block_size ? b->opt.block_size : 512;
     int per_sm = 0;
-    cudaError_t e = b->opt.bfs == BM_GPUBFS_WR
+    cudaError_t e = b->opt.deterministic
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<true, true>, b->block, 0)
+                    : b->opt.bfs == BM_GPUBFS_WR
                         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<true>, b->block, 0)
                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<false>, b->block, 0);
     if (e != cudaSuccess) return batch_fail(b, e);
@@ -243,7 +266,8 @@ int32_t capture(bm_batch* b, int32_t* rmatch, int32_t* cmatch, int greedy) {
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaMemsetAsync(b->ctl, 0, sizeof(BatchCtl), cs);
-        if (b->opt.bfs == BM_GPUBFS_WR) k_batch<true><<<b->grid, b->block, 0, cs>>>(bp);
+        if (b->opt.deterministic) k_batch<true, true><<<b->grid, b->block, 0, cs>>>(bp);
+        else if (b->opt.bfs == BM_GPUBFS_WR) k_batch<true><<<b->grid, b->block, 0, cs>>>(bp);
         else k_batch<false><<<b->grid, b->block, 0, cs>>>(bp);
         e = cudaStreamEndCapture(cs, &b->graph);
     }
@@ -273,6 +297,8 @@ int32_t bm_batch_create(const bm_batch_desc* desc, void* stream, const bm_option
     if (o.mode != BM_APFB && o.mode != BM_APSB) return BM_ERR_INVALID_ARG;
     if (o.bfs != BM_GPUBFS && o.bfs != BM_GPUBFS_WR) return BM_ERR_INVALID_ARG;
     if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 1024 || o.block_size % 32)) return BM_ERR_INVALID_ARG;
+    if (o.deterministic != 0 && o.deterministic != 1) return BM_ERR_INVALID_ARG;
+    if (o.deterministic && (o.bfs != BM_GPUBFS_WR || o.wr_one_endpoint != 1)) return BM_ERR_INVALID_ARG;
     bm_batch* b = new (std::nothrow) bm_batch();
     if (!b) return BM_ERR_NOMEM;
     b->d = *desc;
@@ -325,7 +351,9 @@ int32_t bm_batch_create(const bm_batch_desc* desc, void* stream, const bm_option
     const size_t o_q = off; off += al(8 * C);
     const size_t o_pd = off; off += al(4 * R);
     const size_t o_ep = off; off += al(4 * R);
-    if (cudaMalloc(&b->arena, off) != cudaSuccess || cudaMallocHost((void**)&b->h_ctl, sizeof(BatchCtl)) != cudaSuccess) {
+    const size_t det_bytes = al(8 * C) + al(8 * R) + 4 * R;
+    if (cudaMalloc(&b->arena, off) != cudaSuccess || cudaMallocHost((void**)&b->h_ctl, sizeof(BatchCtl)) != cudaSuccess ||
+        (o.deterministic && cudaMalloc(&b->det_arena, det_bytes) != cudaSuccess)) {
         (void)cudaGetLastError();
         bm_batch_destroy(b);
         return BM_ERR_NOMEM;
@@ -376,6 +404,17 @@ int32_t bm_batch_set_options(bm_batch* b, const bm_options* opt) {
     if (opt->bfs != BM_GPUBFS && opt->bfs != BM_GPUBFS_WR) return BM_ERR_INVALID_ARG;
     if (opt->block_size != 0 && (opt->block_size < 32 || opt->block_size > 1024 || opt->block_size % 32))
         return BM_ERR_INVALID_ARG;
+    if (opt->deterministic != 0 && opt->deterministic != 1) return BM_ERR_INVALID_ARG;
+    if (opt->deterministic && (opt->bfs != BM_GPUBFS_WR || opt->wr_one_endpoint != 1)) return BM_ERR_INVALID_ARG;
+    if (opt->deterministic && !b->det_arena) {
+        const size_t cols = (size_t)(b->total_cols ? b->total_cols : 1), rows = (size_t)(b->total_rows ? b->total_rows : 1);
+        const size_t bytes = ((8 * cols + 255) & ~size_t(255)) + ((8 * rows + 255) & ~size_t(255)) + 4 * rows;
+        if (cudaMalloc(&b->det_arena, bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            b->det_arena = nullptr;
+            return BM_ERR_NOMEM;
+        }
+    }
     b->opt = *opt;
     return configure_batch(b);
 }
@@ -432,6 +471,7 @@ int32_t bm_batch_destroy(bm_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->arena) cudaFree(b->arena);
+    if (b->det_arena) cudaFree(b->det_arena);
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
     (void)cudaGetLastError();
     delete b;

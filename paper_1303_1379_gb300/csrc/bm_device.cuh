@@ -728,7 +728,7 @@ __device__ __forceinline__ void tile_load_det(const Params& p, const int2* queue
                     __stcg(&p.root[c], myroot);
                     __stcg(&p.level[c], lvl);
                     __stcg(&p.pred[row], par);
-                    __stcg(&p.crec[c], make_int2(par, row));
+                    if (p.crec) __stcg(&p.crec[c], make_int2(par, row));
                 }
             }
             if (c >= 0 && !idx_ok(p, myroot, p.nc)) c = -1;
@@ -747,10 +747,11 @@ __device__ __forceinline__ void tile_load_det(const Params& p, const int2* queue
 }
 
 // tile_edges for the deterministic option (the rules above); lvl is the level
-// of the tile's columns, slot the step's counter slot (ecand count).
-template <class PushCol, bool NC = true>
-__device__ __forceinline__ void tile_edges_det(const Params& p, int tw, int lvl, int slot, Smem& sm, Counters& cnt,
-                                               PushCol push_col) {
+// of the tile's columns; push_off(r) lists a row that received its first
+// offer of the level in ecand.
+template <class PushCol, class PushOff, bool NC = true>
+__device__ __forceinline__ void tile_edges_det(const Params& p, int tw, int lvl, Smem& sm, Counters& cnt,
+                                               PushCol push_col, PushOff push_off) {
     const int T = blockDim.x;
     const int t = threadIdx.x;
     const int total = sm.total;
@@ -796,7 +797,7 @@ __device__ __forceinline__ void tile_edges_det(const Params& p, int tw, int lvl,
             } else if (cm[u] == -1) {
                 const unsigned long long want =
                     ((unsigned long long)(unsigned)sm.root[own[u]] << 32) | (unsigned)col;
-                if (atomicMin(&p.ekey[r[u]], want) == DKEY_NONE) push(p.ecand, 0, &p.ctl->dcnt[slot], r[u]);
+                if (atomicMin(&p.ekey[r[u]], want) == DKEY_NONE) push_off(r[u]);
                 sm.has_ep = 1;
             }
         }
@@ -815,6 +816,7 @@ __device__ __forceinline__ void step_expand_det(const Params& p, int2* queue, in
     const int ntiles = (q + tw - 1) / tw;
     const bool narrow = ntiles <= (int)gridDim.x;
     auto push_col = [&](int2 v) { push_block(p, queue, sm, qe, slot, v); };
+    auto push_off = [&](int r) { push(p.ecand, 0, &p.ctl->dcnt[slot], r); };
     if (!narrow) {
         const int G = gridDim.x, T = blockDim.x;
         auto clamp_w = [&](long long w) { return (int)min((long long)T, max(32LL, (w + 31) & ~31LL)); };
@@ -825,7 +827,7 @@ __device__ __forceinline__ void step_expand_det(const Params& p, int2* queue, in
             const int grab = clamp_w(((long long)q - first - width) / (2 * G));
             tile_load_det(p, queue, qb, q, first, width, lvl, sm, cnt, &p.ctl->tcnt[slot], grab, G * w0);
             const int next_first = sm.tile;
-            tile_edges_det(p, width, lvl, slot, sm, cnt, push_col);
+            tile_edges_det(p, width, lvl, sm, cnt, push_col, push_off);
             flush_block(p, queue, sm, qe, slot);
             first = next_first;
             width = grab;
@@ -834,17 +836,16 @@ __device__ __forceinline__ void step_expand_det(const Params& p, int2* queue, in
     }
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {  // block-uniform
         tile_load_det(p, queue, qb, q, tile * tw, tw, lvl, sm, cnt, nullptr);
-        tile_edges_det(p, tw, lvl, slot, sm, cnt, push_col);
+        tile_edges_det(p, tw, lvl, sm, cnt, push_col, push_off);
         flush_block(p, queue, sm, qe, slot);
     }
 }
 
 // After a level with offers (n rows listed in ecand): every listed row
-// offers itself to the root that won it.
-__device__ __forceinline__ void step_det_offer(const Params& p, int n) {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nthr = gridDim.x * blockDim.x;
-    for (int i = tid; i < n; i += nthr) {
+// offers itself to the root that won it.  Entries i0, i0 + stride, ... (the
+// grid, or one block).
+__device__ __forceinline__ void det_offer(const Params& p, int n, int i0, int stride) {
+    for (int i = i0; i < n; i += stride) {
         const int r = __ldcg(&p.ecand[i]);
         if (!idx_ok(p, r, p.nr)) continue;
         const int rho = (int)(__ldcg(&p.ekey[r]) >> 32);
@@ -854,11 +855,11 @@ __device__ __forceinline__ void step_det_offer(const Params& p, int n) {
 }
 
 // Then every root takes the smallest row that offered itself as its one
-// endpoint; every listed row's offer is cleared.
-__device__ __forceinline__ void step_det_take(const Params& p, int n) {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nthr = gridDim.x * blockDim.x;
-    for (int i = tid; i < n; i += nthr) {
+// endpoint (push_end appends it to the endpoint list); every listed row's
+// offer is cleared.
+template <class PushEnd>
+__device__ __forceinline__ void det_take(const Params& p, int n, int i0, int stride, PushEnd push_end) {
+    for (int i = i0; i < n; i += stride) {
         const int r = __ldcg(&p.ecand[i]);
         if (!idx_ok(p, r, p.nr)) continue;
         const unsigned long long k = __ldcg(&p.ekey[r]);
@@ -867,10 +868,17 @@ __device__ __forceinline__ void step_det_take(const Params& p, int n) {
             __stcg(&p.rmatch[r], -2);
             __stcg(&p.pred[r], (int)(unsigned)(k & 0xffffffffull));
             __stcg(&p.level[rho], -r);
-            push(p.endpoints, 0, &p.ctl->ep_phase, r);
+            push_end(r);
         }
         __stcg(&p.ekey[r], DKEY_NONE);
     }
+}
+__device__ __forceinline__ void step_det_offer(const Params& p, int n) {
+    det_offer(p, n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+__device__ __forceinline__ void step_det_take(const Params& p, int n) {
+    det_take(p, n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x,
+             [&](int r) { push(p.endpoints, 0, &p.ctl->ep_phase, r); });
 }
 
 // ------------------------------------------------------------------ Alternate
@@ -1226,6 +1234,201 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
     }
     card_out = card;
     phases_out = phases + (n_roots == 0 ? 1 : 0);  // no root left: Algorithm 1's last search finds nothing
+    levels_out = levels_total;
+    eps_out = eps_total;
+    ins_out = ins_total;
+    __syncthreads();
+    return status;
+}
+
+// ------------------------------------------------------------------ one graph, one block, deterministic
+// The cheap matching of the deterministic option, by one block: rounds in
+// which every unmatched column proposes to the first unmatched row of its
+// list and every proposed row takes the smallest proposer (atomicMin in
+// ekey[r]); until a round without proposals.  Scratch: level (position in
+// the column's list), root (the row proposed to, -1 none); ekey must be all
+// ones before and is again after.
+template <bool NC>
+__device__ __forceinline__ void block_greedy_rounds(const Params& p, Smem& sm) {
+    const int T = blockDim.x, t = threadIdx.x, nc = p.nc;
+    for (int c = t; c < nc; c += T) __stcg(&p.level[c], ld_csr<NC>(&p.col_ptr[c]));
+    for (int round = 0; round <= nc; ++round) {
+        if (t == 0) sm.ok = 0;
+        __syncthreads();
+        bool any = false;
+        for (int c = t; c < nc; c += T) {
+            int want = -1;
+            if (__ldcg(&p.cmatch[c]) == -1) {
+                int pos = __ldcg(&p.level[c]);
+                const int end = ld_csr<NC>(&p.col_ptr[c + 1]);
+                while (pos < end) {  // 4 rows per step, their matches in flight together
+                    int r[4], m[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) r[u] = pos + u < end ? ld_csr<NC>(&p.row_idx[pos + u]) : -1;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) m[u] = (r[u] >= 0 && idx_ok(p, r[u], p.nr)) ? __ldcg(&p.rmatch[r[u]]) : 0;
+                    int k = 0;
+                    while (k < 4 && r[k] >= 0 && m[k] != -1) ++k;
+                    if (k < 4 && r[k] >= 0) { pos += k; want = r[k]; break; }
+                    pos += 4;
+                }
+                if (pos > end) pos = end;
+                __stcg(&p.level[c], pos);
+                if (want >= 0) {
+                    atomicMin(&p.ekey[want], (unsigned long long)(unsigned)c);
+                    any = true;
+                }
+            }
+            __stcg(&p.root[c], want);
+        }
+        if (any) sm.ok = 1;
+        __syncthreads();
+        const bool more = sm.ok != 0;
+        for (int c = t; c < nc; c += T) {
+            const int r = __ldcg(&p.root[c]);
+            if (r >= 0 && __ldcg(&p.ekey[r]) == (unsigned long long)(unsigned)c) {
+                __stcg(&p.rmatch[r], c);
+                __stcg(&p.cmatch[c], r);
+            }
+        }
+        __syncthreads();
+        for (int c = t; c < nc; c += T) {
+            const int r = __ldcg(&p.root[c]);
+            if (r >= 0) __stcg(&p.ekey[r], DKEY_NONE);
+        }
+        __syncthreads();
+        if (!more) break;
+    }
+}
+
+// The whole method on one graph by one block with the deterministic option's
+// rules (GPUBFS-WR, one endpoint per root; p.dkey, p.ekey, p.ecand hold the
+// graph's keys and offer list): the cheap matching in rounds if `greedy`,
+// then Algorithm 1 one level at a time, each level followed -- when it
+// produced offers -- by the two passes that hand rows to roots.  The search
+// trees are disjoint, so Alternate's walks never meet.  Same outputs as
+// block_match_graph; the result depends on the graph and the start only.
+template <bool NC>
+__device__ int block_match_graph_det(const Params& p, int greedy, Smem& sm, Counters& cnt, int& card_out,
+                                     int& phases_out, long long& levels_out, long long& eps_out,
+                                     long long& ins_out) {
+    const int T = blockDim.x;
+    const int t = threadIdx.x;
+    const int nr = p.nr, nc = p.nc;
+    if (t == 0) sm.ok = 0;
+    // ---- rows whose column does not point back are unmatched; every key "none"
+    for (int r = t; r < nr; r += T) {
+        const int m = __ldcg(&p.rmatch[r]);
+        if (m != -1 && (m < 0 || m >= nc || __ldcg(&p.cmatch[m]) != r)) __stcg(&p.rmatch[r], -1);
+        __stcg(&p.ekey[r], DKEY_NONE);
+    }
+    for (int c = t; c < nc; c += T) __stcg(&p.dkey[c], DKEY_NONE);
+    __syncthreads();
+    if (greedy) block_greedy_rounds<NC>(p, sm);
+    const int max_phases = (nr < nc ? nr : nc) + 2;
+    int phases = 0, card = 0, status = 0;
+    long long levels_total = 0, eps_total = 0, ins_total = 0;
+    int free_total = 0, iso_free = 0;
+    block_full_init<true, NC>(p, sm, cnt, free_total, iso_free);
+    int n_roots = sm.qn;
+    for (;;) {
+        card = nc - free_total;
+        if (n_roots == 0) break;
+        if (phases >= max_phases) { status = -4 /*BM_ERR_ITER_LIMIT*/; break; }
+        ++phases;
+        // sm.qn: queue tail; sm.qbase: endpoints; sm.npush: rows listed in ecand this level
+        if (t == 0) { sm.qn = n_roots; sm.qbase = 0; sm.npush = 0; sm.has_ep = 0; }
+        __syncthreads();
+        int qb = 0, qe = n_roots, lvl = L0, levels = 0, n_ep = 0;
+        auto push_col = [&](int2 v) { p.queue[atomicAdd(&sm.qn, 1)] = v; };
+        auto push_off = [&](int r) { p.ecand[atomicAdd(&sm.npush, 1)] = r; };
+        auto push_end = [&](int r) { p.endpoints[atomicAdd(&sm.qbase, 1)] = r; };
+        for (;;) {
+            const int q = qe - qb;
+            for (int first = 0; first < q; first += T) {
+                tile_load_det<NC>(p, p.queue, qb, q, first, T, lvl, sm, cnt, nullptr);
+                tile_edges_det<decltype(push_col), decltype(push_off), NC>(p, T, lvl, sm, cnt, push_col, push_off);
+                __syncthreads();  // sm.off/beg/col/root are reused by the next tile
+            }
+            __syncthreads();
+            const int n_off = sm.npush;
+            const bool found = n_off > 0;
+            if (found) {
+                det_offer(p, n_off, t, T);
+                __syncthreads();
+                det_take(p, n_off, t, T, push_end);
+                __syncthreads();
+                if (t == 0) { sm.npush = 0; sm.has_ep = 0; }
+            }
+            const int tail = sm.qn;
+            const int eps = sm.qbase;
+            __syncthreads();
+            ++levels;
+            ins_total += tail - qe;
+            if (tail == qe) { n_ep = eps; break; }          // no vertex inserted
+            if (p.mode == 1 && found) { n_ep = eps; break; }  // APsB
+            if (levels > nc + 2) { status = -4; n_ep = eps; break; }
+            qb = qe;
+            qe = tail;
+            ++lvl;
+        }
+        const int tail = sm.qn;
+        levels_total += levels;
+        eps_total += n_ep;
+        if (status) break;
+        if (n_ep == 0) break;  // no augmenting path: maximum (Berge)
+        // ---- Alternate (Algorithm 3): disjoint paths, each walked to its root
+        for (int i = t; i < n_ep; i += T) {
+            int r = __ldcg(&p.endpoints[i]);
+            int steps = 0;
+            while (r != -1) {
+                if (++steps > tail + 2) { atomicCAS(&sm.ok, 0, -4); break; }
+                if (!idx_ok(p, r, nr)) { atomicCAS(&sm.ok, 0, -11); break; }
+                const int c = __ldcg(&p.pred[r]);
+                if ((unsigned)c >= (unsigned)nc) { atomicCAS(&sm.ok, 0, -7); break; }
+                const int r2 = __ldcg(&p.cmatch[c]);
+                __stcg(&p.cmatch[c], r);
+                __stcg(&p.rmatch[r], c);
+                cnt.alt++;
+                r = r2;
+            }
+        }
+        __syncthreads();
+        if (sm.ok != 0) { status = sm.ok; break; }
+        // ---- columns inserted by this search go back to "unvisited" ...
+        for (int i = n_roots + t; i < tail; i += T) {
+            const int c = __ldcg(&p.queue[i]).x;
+            if (!idx_ok(p, c, nc)) continue;
+            __stcg(&p.level[c], L0 - 1);
+            __stcg(&p.root[c], -1);
+            __stcg(&p.dkey[c], DKEY_NONE);
+        }
+        // ... and the roots that are still unmatched stay roots (compacted in place)
+        int kept = 0;
+        for (int base = 0; base < n_roots; base += T) {
+            const int i = base + t;
+            int c = -1, keep = 0;
+            if (i < n_roots) {
+                c = __ldcg(&p.queue[i]).x;
+                if (!idx_ok(p, c, nc)) c = 0;  // checked build only: recorded, and column 0 is harmless here
+                keep = __ldcg(&p.cmatch[c]) < 0;
+                __stcg(&p.dkey[c], DKEY_NONE);
+                if (!keep) {
+                    __stcg(&p.level[c], L0 - 1);
+                    __stcg(&p.root[c], -1);
+                }
+            }
+            const int pos = block_exclusive_scan(keep, sm);
+            const int chunk = sm.total;
+            if (keep) p.queue[kept + pos] = make_int2(c, c);
+            kept += chunk;
+            __syncthreads();
+        }
+        n_roots = kept;
+        free_total = iso_free + kept;
+    }
+    card_out = card;
+    phases_out = phases + (n_roots == 0 ? 1 : 0);
     levels_out = levels_total;
     eps_out = eps_total;
     ins_out = ins_total;

@@ -127,3 +127,56 @@ def test_full_size_workloads_same_as_the_oracle(name):
     # the benchmark's graphs at full size, from the oracle's greedy start
     g = synth.workload(name)
     check_same_as_oracle(g, start(g, "greedy"), False)
+
+
+# ------------------------------------------------------------ batched path
+def oracle_batch_det(b, greedy):
+    """Per graph: the cheap matching in rounds (if greedy), then the method
+    with the same rules; returns the concatenated arrays and summed counters."""
+    R, C = int(b.row_off[-1]), int(b.col_off[-1])
+    rm_all = np.full(R, -1, np.int32)
+    cm_all = np.full(C, -1, np.int32)
+    tot = dict.fromkeys(STATS, 0)
+    for k in range(b.n_graphs):
+        g = b.graph(k)
+        rm0 = cm0 = None
+        if greedy:
+            rm0, cm0, _, _ = oracle.greedy_rounds(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+        rm, cm, _, st = oracle.apfb_wr_det(g.n_rows, g.n_cols, g.col_ptr, g.row_idx, rm0, cm0)
+        rm_all[b.row_off[k]:b.row_off[k + 1]] = rm
+        cm_all[b.col_off[k]:b.col_off[k + 1]] = cm
+        for key in STATS:
+            tot[key] += st[key]
+    return rm_all, cm_all, tot
+
+
+def run_batch_det(b, greedy, **options):
+    from paper_1303_1379_gb300 import bmatch
+    R, C = int(b.row_off[-1]), int(b.col_off[-1])
+    rm = torch.full((max(R, 1),), -1, dtype=torch.int32, device="cuda")
+    cm = torch.full((max(C, 1),), -1, dtype=torch.int32, device="cuda")
+    with bmatch.Batch.from_synth(b, deterministic=1, **options) as bb:
+        rc, st = bb.match(rm, cm, greedy=greedy)
+        status, _ = bb.graph_status()
+    assert rc == 0 and np.all(status == 0)
+    return rm[:R].cpu().numpy(), cm[:C].cpu().numpy(), st
+
+
+@pytest.mark.parametrize("greedy", [True, False], ids=["rounds-greedy", "empty"])
+def test_batch_same_as_the_oracle_graph_by_graph(greedy):
+    b = synth.batch_graphs(96, seed=41, nr_lo=10, nr_hi=4000, mu_lo=1.5, mu_hi=8.0)
+    w_rm, w_cm, w_st = oracle_batch_det(b, greedy)
+    rm, cm, st = run_batch_det(b, greedy)
+    np.testing.assert_array_equal(rm, w_rm)
+    np.testing.assert_array_equal(cm, w_cm)
+    # the batch reports phases, levels, ... summed over its graphs; roots are not counted there
+    assert {k: st[k] for k in STATS if k != "roots"} == {k: v for k, v in w_st.items() if k != "roots"}
+
+
+@pytest.mark.parametrize("block,per_sm", [(64, 0), (256, 1), (1024, 1)])
+def test_batch_same_for_every_geometry(block, per_sm):
+    b = synth.batch_graphs(48, seed=42, nr_lo=10, nr_hi=6000)
+    w_rm, w_cm, _ = oracle_batch_det(b, True)
+    rm, cm, _ = run_batch_det(b, True, block_size=block, blocks_per_sm=per_sm)
+    np.testing.assert_array_equal(rm, w_rm)
+    np.testing.assert_array_equal(cm, w_cm)
