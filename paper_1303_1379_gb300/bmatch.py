@@ -40,7 +40,8 @@ class bm_server_options(ctypes.Structure):
                 ("bfs", ctypes.c_int32), ("keep_results", ctypes.c_int32),
                 ("idle_timeout_ns", ctypes.c_int64), ("poll_interval_us", ctypes.c_int32),
                 ("exclusive_alongside", ctypes.c_int32), ("exclusive_min_edges", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 3)]
+                ("deterministic", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 2)]
 
 
 class bm_request_info(ctypes.Structure):

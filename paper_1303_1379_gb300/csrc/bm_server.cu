@@ -55,6 +55,7 @@ struct SlotDesc {
     long long id;
     long long nnz;
     long long off_cp, off_ri, off_rm, off_cm, off_lv, off_rt, off_q, off_pd, off_ep;  // bytes into the pool
+    long long off_dk, off_ek, off_ec;  // deterministic option's keys and offer list
     int32_t nr, nc;
     int32_t greedy;
     int32_t pad;
@@ -108,7 +109,9 @@ __device__ __forceinline__ void st_release_sys_s32(int32_t* p, int v) {
     asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <bool WR>
+// DET: every request with the deterministic option's rules
+// (block_match_graph_det).
+template <bool WR, bool DET = false>
 __global__ void __launch_bounds__(1024, 1) k_serve(ServeParams sp) {
     __shared__ Smem sm;
     __shared__ long long s_ticket;
@@ -154,6 +157,11 @@ __global__ void __launch_bounds__(1024, 1) k_serve(ServeParams sp) {
                 s_d.off_q = ld_relaxed_sys_s64(&d->off_q);
                 s_d.off_pd = ld_relaxed_sys_s64(&d->off_pd);
                 s_d.off_ep = ld_relaxed_sys_s64(&d->off_ep);
+                if (DET) {
+                    s_d.off_dk = ld_relaxed_sys_s64(&d->off_dk);
+                    s_d.off_ek = ld_relaxed_sys_s64(&d->off_ek);
+                    s_d.off_ec = ld_relaxed_sys_s64(&d->off_ec);
+                }
                 s_d.nr = ld_relaxed_sys_s32(&d->nr);
                 s_d.nc = ld_relaxed_sys_s32(&d->nc);
                 s_d.greedy = ld_relaxed_sys_s32(&d->greedy);
@@ -187,7 +195,14 @@ __global__ void __launch_bounds__(1024, 1) k_serve(ServeParams sp) {
             for (int r = threadIdx.x; r < p.nr; r += blockDim.x) __stcg(&p.rmatch[r], -1);
             for (int c = threadIdx.x; c < p.nc; c += blockDim.x) __stcg(&p.cmatch[c], -1);
             __syncthreads();
-            status = bmd::block_match_graph<WR, false>(p, s_d.greedy, sm, cnt, card, phases, levels, eps, ins);
+            if constexpr (DET) {
+                p.dkey = (unsigned long long*)(sp.pool + s_d.off_dk);
+                p.ekey = (unsigned long long*)(sp.pool + s_d.off_ek);
+                p.ecand = (int32_t*)(sp.pool + s_d.off_ec);
+                status = bmd::block_match_graph_det<false>(p, s_d.greedy, sm, cnt, card, phases, levels, eps, ins);
+            } else {
+                status = bmd::block_match_graph<WR, false>(p, s_d.greedy, sm, cnt, card, phases, levels, eps, ins);
+            }
         }
         if (threadIdx.x == 0) {
             SlotDone* d = &sp.done[t % sp.ring];
@@ -224,13 +239,14 @@ struct Request {
 
 size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
-constexpr int kOffs = 13;      // arrays of a request's pool region
+constexpr int kOffs = 16;      // arrays of a request's pool region
 constexpr int kExclSlots = 64;  // whole-GPU runs queued at once
 
 // A request's region: its CSR, matching and the workspace of the worker
 // routine (offsets 0-8); requests with at least exclusive_min_edges edges also
-// get the rest of a whole-GPU launch's workspace (9-12).
-size_t request_bytes(int32_t nr, int32_t nc, long long nnz, bool exclusive, size_t* offs) {
+// get the rest of a whole-GPU launch's workspace (9-12); with the
+// deterministic option, the keys and the offer list (13-15).
+size_t request_bytes(int32_t nr, int32_t nc, long long nnz, bool exclusive, bool det, size_t* offs) {
     const size_t NR = (size_t)(nr ? nr : 1), NC = (size_t)(nc ? nc : 1);
     size_t o = 0;
     offs[0] = o; o += round256(4 * ((size_t)nc + 1));       // col_ptr
@@ -248,6 +264,12 @@ size_t request_bytes(int32_t nr, int32_t nc, long long nnz, bool exclusive, size
         offs[10] = o; o += round256(4 * NR);                  // claim stamps
         offs[11] = o; o += round256(8 * NC);                  // Alternate records
         offs[12] = o; o += round256(sizeof(bmd::Ctl));        // control block
+    }
+    offs[13] = offs[14] = offs[15] = o;
+    if (det) {
+        offs[13] = o; o += round256(8 * NC);                  // tree-entry keys
+        offs[14] = o; o += round256(8 * NR);                  // offer keys
+        offs[15] = o; o += round256(4 * NR);                  // rows offered during a level
     }
     return o;
 }
@@ -312,7 +334,8 @@ void launch_workers(bm_server* s) {
     sp.mode = s->opt.mode;
     sp.one_ep = 1;
     sp.idle_ns = s->opt.idle_timeout_ns;
-    if (s->opt.bfs == BM_GPUBFS_WR) k_serve<true><<<s->grid, s->block, 0, s->work_stream>>>(sp);
+    if (s->opt.deterministic) k_serve<true, true><<<s->grid, s->block, 0, s->work_stream>>>(sp);
+    else if (s->opt.bfs == BM_GPUBFS_WR) k_serve<true><<<s->grid, s->block, 0, s->work_stream>>>(sp);
     else k_serve<false><<<s->grid, s->block, 0, s->work_stream>>>(sp);
     if (cudaGetLastError() != cudaSuccess) { s->sticky = BM_ERR_CUDA; return; }
     cudaEventRecord(s->worker_ev, s->work_stream);
@@ -323,7 +346,7 @@ void launch_workers(bm_server* s) {
 // A request large enough to run alone on the whole GPU (the persistent
 // single-graph kernel) rather than on one worker block.
 bool is_exclusive(const bm_server* s, const Request& r) {
-    return s->opt.exclusive_min_edges > 0 && r.nnz >= s->opt.exclusive_min_edges;
+    return !s->opt.deterministic && s->opt.exclusive_min_edges > 0 && r.nnz >= s->opt.exclusive_min_edges;
 }
 
 // Starts request r alone on the whole GPU: the workers are told to leave, and
@@ -331,7 +354,7 @@ bool is_exclusive(const bm_server* s, const Request& r) {
 // the copy of its control block and an event.  Returns BM_OK or an error.
 int32_t start_exclusive(bm_server* s, Request& r, int slot) {
     size_t offs[kOffs];
-    request_bytes(r.nr, r.nc, r.nnz, true, offs);
+    request_bytes(r.nr, r.nc, r.nnz, true, false, offs);
     unsigned char* b = s->pool + r.off;
     bmd::Params p{};
     p.nr = r.nr;
@@ -436,7 +459,7 @@ bool schedule_once(bm_server* s) {
         if (s->ring_owner[slot] != -1) break;  // ticket next_ticket - ring still running
         const long long ticket = s->next_ticket++;
         size_t offs[kOffs];
-        request_bytes(r.nr, r.nc, r.nnz, false, offs);
+        request_bytes(r.nr, r.nc, r.nnz, false, s->opt.deterministic != 0, offs);
         SlotDesc& d = s->desc[slot];
         d.id = r.id;
         d.nnz = r.nnz;
@@ -449,6 +472,9 @@ bool schedule_once(bm_server* s) {
         d.off_q = (long long)(r.off + offs[6]);
         d.off_pd = (long long)(r.off + offs[7]);
         d.off_ep = (long long)(r.off + offs[8]);
+        d.off_dk = (long long)(r.off + offs[13]);
+        d.off_ek = (long long)(r.off + offs[14]);
+        d.off_ec = (long long)(r.off + offs[15]);
         d.nr = r.nr;
         d.nc = r.nc;
         d.greedy = r.greedy;
@@ -465,7 +491,7 @@ bool schedule_once(bm_server* s) {
         Request& r = s->reqs[id];
         if (r.state == CANCELLED) { s->pending.pop_front(); continue; }
         size_t offs[kOffs];
-        r.bytes = request_bytes(r.nr, r.nc, r.nnz, is_exclusive(s, r), offs);
+        r.bytes = request_bytes(r.nr, r.nc, r.nnz, is_exclusive(s, r), s->opt.deterministic != 0, offs);
         if (r.bytes > s->alloc->size()) {  // can never fit
             r.state = DONE;
             r.status = BM_ERR_TOO_LARGE;
@@ -545,7 +571,8 @@ int32_t bm_server_create(const bm_server_options* opt, bm_server** out) {
         o.block_size % 32 || o.blocks_per_sm < 1 || o.pool_bytes < 0 || o.reserve_bytes < 0 ||
         o.idle_timeout_ns <= 0 || o.poll_interval_us < 0 || o.exclusive_min_edges < 0 ||
         (o.mode != BM_APFB && o.mode != BM_APSB) ||
-        (o.bfs != BM_GPUBFS && o.bfs != BM_GPUBFS_WR))
+        (o.bfs != BM_GPUBFS && o.bfs != BM_GPUBFS_WR) || (o.deterministic != 0 && o.deterministic != 1) ||
+        (o.deterministic && o.bfs != BM_GPUBFS_WR))
         return BM_ERR_INVALID_ARG;
     bm_server* s = new (std::nothrow) bm_server();
     if (!s) return BM_ERR_NOMEM;
@@ -557,7 +584,8 @@ int32_t bm_server_create(const bm_server_options* opt, bm_server** out) {
         return fail(BM_ERR_CUDA);
     }
     int per_sm = 0;
-    if ((o.bfs == BM_GPUBFS_WR ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve<true>, o.block_size, 0)
+    if ((o.deterministic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve<true, true>, o.block_size, 0)
+         : o.bfs == BM_GPUBFS_WR ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve<true>, o.block_size, 0)
                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve<false>, o.block_size, 0)) != cudaSuccess) {
         (void)cudaGetLastError();
         return fail(BM_ERR_CUDA);
@@ -565,7 +593,7 @@ int32_t bm_server_create(const bm_server_options* opt, bm_server** out) {
     if (per_sm < 1) return fail(BM_ERR_UNSUPPORTED);
     s->block = o.block_size;
     // alongside: one worker block per SM, leaving the other half of each SM to the whole-GPU lane
-    const int bps = o.exclusive_alongside ? 1 : (o.blocks_per_sm < per_sm ? o.blocks_per_sm : per_sm);
+    const int bps = (o.exclusive_alongside && !o.deterministic) ? 1 : (o.blocks_per_sm < per_sm ? o.blocks_per_sm : per_sm);
     s->grid = s->num_sms * bps;
     size_t pool = (size_t)o.pool_bytes;
     if (pool == 0) {

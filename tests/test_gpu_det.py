@@ -180,3 +180,58 @@ def test_batch_same_for_every_geometry(block, per_sm):
     rm, cm, _ = run_batch_det(b, True, block_size=block, blocks_per_sm=per_sm)
     np.testing.assert_array_equal(rm, w_rm)
     np.testing.assert_array_equal(cm, w_cm)
+
+
+# ------------------------------------------------------------ served path
+def served_requests():
+    """Uniform and R-MAT requests of 50 to 20,000 rows, and one R-MAT request
+    of about 700 k edges (above the default threshold for the single-graph
+    lane; with the option every request runs on a worker block)."""
+    rng = np.random.default_rng(77)
+    out = []
+    for i in range(24):
+        nr = int(np.exp(rng.uniform(np.log(50), np.log(20000))))
+        nc = max(1, int(round(nr * rng.uniform(0.8, 1.25))))
+        mu = rng.uniform(3, 16)
+        if i % 2 == 0:
+            out.append(synth.uniform_graph(nr, nc, max(1, int(round(2 * mu - 1))), seed=3000 + i))
+        else:
+            n = max(nr, nc)
+            out.append(synth.rmat_graph(int(np.ceil(np.log2(max(n, 2)))), int(n * mu), seed=3000 + i, n=n))
+    out.append(synth.rmat_graph(17, 800_000, seed=3999))
+    return out
+
+
+def test_served_results_equal_the_oracle_alone_and_in_the_mix():
+    from paper_1303_1379_gb300 import bmatch
+    reqs = served_requests()
+    want = []
+    for g in reqs:
+        rm0, cm0, _, _ = oracle.greedy_rounds(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+        rm, cm, card, _ = oracle.apfb_wr_det(g.n_rows, g.n_cols, g.col_ptr, g.row_idx, rm0, cm0)
+        want.append((rm, cm, card))
+    assert reqs[-1].nnz >= 524_288
+
+    def fetch(srv, rid, g):
+        info = srv.wait(rid)
+        assert info["state"] == bmatch.BM_REQ_DONE and info["status"] == 0
+        rm = np.empty(g.n_rows, np.int32)
+        cm = np.empty(g.n_cols, np.int32)
+        srv.fetch(rid, rm, cm)
+        srv.release(rid)
+        return rm, cm, info["card"]
+
+    with bmatch.Server(keep_results=1, pool_bytes=1 << 30, deterministic=1) as srv:
+        for g, w in zip(reqs[:8] + reqs[-1:], want[:8] + want[-1:]):  # alone, one at a time
+            rm, cm, card = fetch(srv, srv.submit(g.n_rows, g.n_cols, g.col_ptr, g.row_idx), g)
+            assert card == w[2]
+            np.testing.assert_array_equal(rm, w[0])
+            np.testing.assert_array_equal(cm, w[1])
+        ids = [srv.submit(g.n_rows, g.n_cols, g.col_ptr, g.row_idx) for g in reqs]  # the mix
+        for g, w, rid in zip(reqs, want, ids):
+            rm, cm, card = fetch(srv, rid, g)
+            assert card == w[2]
+            np.testing.assert_array_equal(rm, w[0])
+            np.testing.assert_array_equal(cm, w[1])
+        st = srv.stats()
+        assert st["exclusive_runs"] == 0 and st["pool_used"] == 0
