@@ -100,9 +100,11 @@ typedef struct bm_options {
                               smallest row offered to it as its one endpoint, the other rows
                               stay unmatched; a root served at level L stops at level L+1.
                               bm_match, bm_match_from and bm_bfs then return the same
-                              matching and counters on every run and for every block size
-                              (bm_greedy stays racy: install a fixed start for a fixed
-                              result).  Needs the persistent driver, GPUBFS-WR and
+                              matching and counters on every run and for every block size,
+                              and bm_greedy runs the cheap matching in rounds: every
+                              unmatched column proposes to the first unmatched row of its
+                              list, every proposed row takes the smallest proposing column,
+                              until no column proposes.  Needs the persistent driver, GPUBFS-WR and
                               wr_one_endpoint = 1 (BM_ERR_INVALID_ARG otherwise); the
                               context allocates 8*n_cols + 12*n_rows bytes on its first
                               deterministic call (BM_ERR_NOMEM if that fails).  0 = default */
@@ -176,7 +178,11 @@ BM_API int32_t bm_set_options(bm_ctx *ctx, const bm_options *opt);
  * each; up to 2048: a warp each, longer: a block each, dealt from lists the
  * first pass builds in the context's queue).  The result is a
  * maximal matching added to the installed one; which maximal matching it is
- * depends on thread timing.  *card_out (host, nullable) gets |M|. */
+ * depends on thread timing.  With the deterministic option the rounds of
+ * proposals described there run instead (one cooperative launch; a barrier
+ * wait that runs out of time returns BM_ERR_TIMEOUT), and the result depends
+ * on the graph and the installed matching only.  *card_out (host, nullable)
+ * gets |M|. */
 BM_API int32_t bm_greedy(bm_ctx *ctx, int32_t *card_out);
 
 /* Installs an initial matching (Section 3: "any prior matching is given in

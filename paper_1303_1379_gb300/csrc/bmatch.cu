@@ -469,6 +469,72 @@ void launch_greedy(int nc, const int32_t* cp, const int32_t* ri, int32_t* rm, in
     k_greedy_heavy<<<grid, block, 0, st>>>(cp, ri, rm, cm, gl, ctl);
 }
 
+// The cheap matching of the deterministic option over the whole GPU (one
+// cooperative launch): rounds in which every unmatched column proposes to the
+// first unmatched row of its list and every proposed row takes the smallest
+// proposing column (atomicMin in ekey[r]), until a round without proposals.
+// Scratch: level (per column: position in its list), root (per column: the
+// row proposed to, -1 none); ekey is all ones before and after.  A column is
+// always handled by the same thread, so its scratch needs no barrier.
+__global__ void __launch_bounds__(1024, 1) k_greedy_rounds(Params p) {
+    using namespace bmd;
+    __shared__ Smem sm;
+    if (threadIdx.x == 0) { sm.qn = 0; sm.npush = 0; sm.has_ep = 0; }
+    int bid = 0;
+    const unsigned long long deadline = globaltimer() + (unsigned long long)p.total_ns;
+    if (ld_volatile(&p.ctl->err) != 0) return;  // CSR check failed before launch
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthr = gridDim.x * blockDim.x;
+    int32_t* pos = p.level;
+    int32_t* want = p.root;
+    for (int c = tid; c < p.nc; c += nthr) __stcg(&pos[c], __ldg(&p.col_ptr[c]));
+    for (int round = 0; round <= p.nc; ++round) {
+        bool any = false;
+        for (int c = tid; c < p.nc; c += nthr) {
+            int w = -1;
+            if (__ldcg(&p.cmatch[c]) == -1) {
+                int at = __ldcg(&pos[c]);
+                const int end = __ldg(&p.col_ptr[c + 1]);
+                while (at < end) {  // 4 rows per step, their matches in flight together
+                    int r[4], m[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) r[u] = at + u < end ? __ldg(&p.row_idx[at + u]) : -1;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) m[u] = (r[u] >= 0 && idx_ok(p, r[u], p.nr)) ? __ldcg(&p.rmatch[r[u]]) : 0;
+                    int k = 0;
+                    while (k < 4 && r[k] >= 0 && m[k] != -1) ++k;
+                    if (k < 4 && r[k] >= 0) { at += k; w = r[k]; break; }
+                    at += 4;
+                }
+                if (at > end) at = end;
+                __stcg(&pos[c], at);
+                if (w >= 0) {
+                    atomicMin(&p.ekey[w], (unsigned long long)(unsigned)c);
+                    any = true;
+                }
+            }
+            __stcg(&want[c], w);
+        }
+        if (any) sm.has_ep = 1;
+        if (!grid_sync(p.ctl, bid, p.wait_ns, deadline, sm, nullptr)) return;
+        const bool more = sm.bc_b > 0;  // some block proposed
+        for (int c = tid; c < p.nc; c += nthr) {
+            const int w = __ldcg(&want[c]);
+            if (w >= 0 && __ldcg(&p.ekey[w]) == (unsigned long long)(unsigned)c) {
+                __stcg(&p.rmatch[w], c);
+                __stcg(&p.cmatch[c], w);
+            }
+        }
+        if (!grid_sync(p.ctl, bid, p.wait_ns, deadline, sm, nullptr)) return;
+        for (int c = tid; c < p.nc; c += nthr) {
+            const int w = __ldcg(&want[c]);
+            if (w >= 0) __stcg(&p.ekey[w], DKEY_NONE);
+        }
+        if (!grid_sync(p.ctl, bid, p.wait_ns, deadline, sm, nullptr)) return;
+        if (!more) break;
+    }
+}
+
 __global__ void k_count_matched(int nc, const int32_t* __restrict__ cm, Ctl* ctl) {
     int n = 0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
@@ -508,7 +574,8 @@ struct bm_ctx {
     int32_t sticky = 0;
     int device = 0;
     int num_sms = 0;
-    int coop_grid[3] = {0, 0, 0};  // blocks of k_match<false, true>, <true, true>, <true, true, true>
+    int coop_grid[4] = {0, 0, 0, 0};  // blocks of k_match<false, true>, <true, true>, <true, true, true>;
+                                      // k_greedy_rounds
     int block = kDefaultBlock;
     // deterministic option: allocated on its first use, [dkey nc][ekey nr][ecand nr]
     void* det_arena = nullptr;
@@ -556,10 +623,11 @@ int grid_for(bm_ctx* ctx, int n) {  // plain launches: enough blocks to fill the
 
 int32_t configure(bm_ctx* ctx) {
     ctx->block = ctx->opt.block_size ? ctx->opt.block_size : kDefaultBlock;
-    for (int wr = 0; wr < 3; ++wr) {
+    for (int wr = 0; wr < 4; ++wr) {
         int per_sm = 0;
         cudaError_t e =
-            wr == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true, true, true>, ctx->block, 0)
+            wr == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy_rounds, ctx->block, 0)
+            : wr == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true, true, true>, ctx->block, 0)
             : wr    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true, true>, ctx->block, 0)
                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<false, true>, ctx->block, 0);
         if (e != cudaSuccess) return cuda_fail(ctx, e);
@@ -725,6 +793,24 @@ int32_t run_host_loop(bm_ctx* ctx, const Params& p) {
     return sync_ctl(ctx);
 }
 
+// The deterministic option's arrays, allocated on first use: [dkey nc][ekey nr][ecand nr].
+int32_t ensure_det_arena(bm_ctx* ctx) {
+    if (ctx->det_arena) return BM_OK;
+    const size_t nr1 = (size_t)(ctx->nr ? ctx->nr : 1), nc1 = (size_t)(ctx->nc ? ctx->nc : 1);
+    const size_t off_ek = (8 * nc1 + 255) & ~size_t(255);
+    const size_t off_ec = off_ek + ((8 * nr1 + 255) & ~size_t(255));
+    if (cudaMalloc(&ctx->det_arena, off_ec + 4 * nr1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        ctx->det_arena = nullptr;
+        return BM_ERR_NOMEM;
+    }
+    char* a = (char*)ctx->det_arena;
+    ctx->dkey = (unsigned long long*)a;
+    ctx->ekey = (unsigned long long*)(a + off_ek);
+    ctx->ecand = (int32_t*)(a + off_ec);
+    return BM_OK;
+}
+
 // Runs the method (or one BFS) on the installed matching.  The control block
 // is cleared by the caller beforehand so that input checks queued before can
 // report through it.
@@ -747,22 +833,11 @@ int32_t run(bm_ctx* ctx, bool bfs_only) {
     ctx->stamp_next += span;
     void* args[] = {&p};
     if (ctx->opt.deterministic) {
-        const size_t nr1 = (size_t)(ctx->nr ? ctx->nr : 1), nc1 = (size_t)(ctx->nc ? ctx->nc : 1);
-        const size_t off_ek = (8 * nc1 + 255) & ~size_t(255);
-        const size_t off_ec = off_ek + ((8 * nr1 + 255) & ~size_t(255));
-        if (!ctx->det_arena) {
-            if (cudaMalloc(&ctx->det_arena, off_ec + 4 * nr1) != cudaSuccess) {
-                (void)cudaGetLastError();
-                ctx->det_arena = nullptr;
-                return BM_ERR_NOMEM;
-            }
-            char* a = (char*)ctx->det_arena;
-            ctx->dkey = (unsigned long long*)a;
-            ctx->ekey = (unsigned long long*)(a + off_ek);
-            ctx->ecand = (int32_t*)(a + off_ec);
-        }
+        int32_t rc = ensure_det_arena(ctx);
+        if (rc) return rc;
         // every key "none" (all ones) at launch; the kernel restores that between phases
-        BM_CUDA(ctx, cudaMemsetAsync(ctx->det_arena, 0xff, off_ec, ctx->stream));
+        BM_CUDA(ctx, cudaMemsetAsync(ctx->det_arena, 0xff, (size_t)((char*)ctx->ecand - (char*)ctx->det_arena),
+                                     ctx->stream));
         p.dkey = ctx->dkey;
         p.ekey = ctx->ekey;
         p.ecand = ctx->ecand;
@@ -988,7 +1063,18 @@ int32_t bm_greedy(bm_ctx* ctx, int32_t* card_out) {
     if (ctx->sticky || !ctx->csr_ready) return BM_ERR_STATE;
     cudaStream_t st = ctx->stream;
     BM_CUDA(ctx, cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), st));
-    if (ctx->nc) {
+    if (ctx->nc && ctx->opt.deterministic) {
+        // proposal rounds: the same matching on every run and launch geometry
+        int32_t rc = ensure_det_arena(ctx);
+        if (rc) return rc;
+        BM_CUDA(ctx, cudaMemsetAsync(ctx->ekey, 0xff, 8 * (size_t)(ctx->nr ? ctx->nr : 1), st));
+        Params p = make_params(ctx, false);
+        p.ekey = ctx->ekey;
+        void* args[] = {&p};
+        BM_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)k_greedy_rounds, ctx->coop_grid[3], ctx->block, args, 0, st));
+        k_count_matched<<<grid_for(ctx, ctx->nc), ctx->block, 0, st>>>(ctx->nc, ctx->cmatch, ctx->ctl);
+        BM_CUDA(ctx, cudaGetLastError());
+    } else if (ctx->nc) {
         launch_greedy(ctx->nc, ctx->col_ptr, ctx->row_idx, ctx->rmatch, ctx->cmatch, nullptr, (int32_t*)ctx->queue,
                       &ctx->ctl->qcnt[0], grid_for(ctx, ctx->nc), ctx->block, st);
         BM_CUDA(ctx, cudaGetLastError());
@@ -997,6 +1083,10 @@ int32_t bm_greedy(bm_ctx* ctx, int32_t* card_out) {
     }
     int32_t rc = sync_ctl(ctx);
     if (rc) return rc;
+    if (ctx->h_ctl->err) {  // a barrier wait of the rounds ran out of time
+        ctx->sticky = ctx->h_ctl->err;
+        return ctx->h_ctl->err;
+    }
     if (card_out) *card_out = ctx->h_ctl->card;
     return BM_OK;
 }

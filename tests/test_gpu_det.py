@@ -235,3 +235,41 @@ def test_served_results_equal_the_oracle_alone_and_in_the_mix():
             np.testing.assert_array_equal(cm, w[1])
         st = srv.stats()
         assert st["exclusive_runs"] == 0 and st["pool_used"] == 0
+
+
+# ------------------------------------------------------------ cheap matching in rounds
+@pytest.mark.parametrize("name", ["uniform-ragged", "rmat15", "rmat17-rcp", "stencil150"])
+def test_cheap_matching_in_rounds_equals_the_oracle(name):
+    from paper_1303_1379_gb300 import bmatch
+    from helpers import to_dev
+    g = graph(name)
+    w_rm, w_cm, w_card, _ = oracle.greedy_rounds(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+    f_rm, f_cm, f_card, f_st = oracle.apfb_wr_det(g.n_rows, g.n_cols, g.col_ptr, g.row_idx, w_rm, w_cm)
+    cp, ri = to_dev(g)
+    for block in (128, 512, 1024):
+        m = bmatch.Matcher(g.n_rows, g.n_cols, g.nnz, cp, ri, deterministic=1, block_size=block)
+        try:
+            assert m.greedy() == w_card
+            rm = torch.empty(g.n_rows, dtype=torch.int32, device="cuda")
+            cm = torch.empty(g.n_cols, dtype=torch.int32, device="cuda")
+            m.get_matching(rm, cm)
+            np.testing.assert_array_equal(rm.cpu().numpy(), w_rm)
+            np.testing.assert_array_equal(cm.cpu().numpy(), w_cm)
+            res = m.match(rm, cm)  # cheap matching + search: the oracle's end to end
+            assert res.card == f_card and {k: res.stats[k] for k in STATS} == f_st
+            np.testing.assert_array_equal(rm.cpu().numpy(), f_rm)
+        finally:
+            m.close()
+
+
+def test_full_size_cheap_matching_in_rounds():
+    from paper_1303_1379_gb300 import bmatch
+    from helpers import to_dev
+    g = synth.workload("rmat21")
+    w_rm, _, w_card, _ = oracle.greedy_rounds(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+    cp, ri = to_dev(g)
+    with bmatch.Matcher(g.n_rows, g.n_cols, g.nnz, cp, ri, deterministic=1) as m:
+        assert m.greedy() == w_card
+        rm = torch.empty(g.n_rows, dtype=torch.int32, device="cuda")
+        m.get_matching(rm, None)
+        np.testing.assert_array_equal(rm.cpu().numpy(), w_rm)
