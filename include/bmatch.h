@@ -381,11 +381,11 @@ typedef struct bm_server_options {
                                     block; 0 = never (default 524,288)                        */
     int32_t deterministic;   /* 1: every request runs with bm_options.deterministic's rules, its
                                 cheap matching in rounds of proposals (each row takes the smallest
-                                proposing column): a request's matching depends on its graph
-                                only, alone or in any mix.  Every request then runs on a worker
-                                block (exclusive_min_edges is not used) and takes
-                                8*n_cols + 12*n_rows more bytes of the pool.  Needs
-                                bfs = BM_GPUBFS_WR.  0 = default                            */
+                                proposing column), on a worker block or on the single-graph
+                                kernel alike: a request's matching depends on its graph only,
+                                alone or in any mix.  Each request takes 8*n_cols + 12*n_rows
+                                more bytes of the pool.  Needs bfs = BM_GPUBFS_WR.
+                                0 = default                                                 */
     int32_t reserved0;
     int64_t reserved[2];
 } bm_server_options;

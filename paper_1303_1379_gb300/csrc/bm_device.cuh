@@ -1245,22 +1245,35 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
 // The cheap matching of the deterministic option, by one block: rounds in
 // which every unmatched column proposes to the first unmatched row of its
 // list and every proposed row takes the smallest proposer (atomicMin in
-// ekey[r]); until a round without proposals.  Scratch: level (position in
-// the column's list), root (the row proposed to, -1 none); ekey must be all
-// ones before and is again after.
+// ekey[r]); until a round without proposals.  Columns of more than 32 rows
+// look for their row a warp at a time (32 rows per step, a ballot of the free
+// ones), from a list in the queue buffer; the others a thread each.
+// Scratch: level (position in the column's list), root (the row proposed to,
+// -1 none); ekey must be all ones before and is again after.
 template <bool NC>
 __device__ __forceinline__ void block_greedy_rounds(const Params& p, Smem& sm) {
     const int T = blockDim.x, t = threadIdx.x, nc = p.nc;
-    for (int c = t; c < nc; c += T) __stcg(&p.level[c], ld_csr<NC>(&p.col_ptr[c]));
+    const int lane = t & 31, warp = t >> 5, nwarps = (T + 31) >> 5;
+    int32_t* longs = (int32_t*)p.queue;
+    if (t == 0) sm.tile = 0;
+    __syncthreads();
+    for (int c = t; c < nc; c += T) {
+        const int b = ld_csr<NC>(&p.col_ptr[c]);
+        __stcg(&p.level[c], b);
+        if (ld_csr<NC>(&p.col_ptr[c + 1]) - b > 32) longs[atomicAdd(&sm.tile, 1)] = c;
+    }
+    __syncthreads();
+    const int nlong = sm.tile;
     for (int round = 0; round <= nc; ++round) {
         if (t == 0) sm.ok = 0;
         __syncthreads();
         bool any = false;
-        for (int c = t; c < nc; c += T) {
+        for (int c = t; c < nc; c += T) {  // short lists: a thread each
+            const int end = ld_csr<NC>(&p.col_ptr[c + 1]);
+            if (end - ld_csr<NC>(&p.col_ptr[c]) > 32) continue;
             int want = -1;
             if (__ldcg(&p.cmatch[c]) == -1) {
                 int pos = __ldcg(&p.level[c]);
-                const int end = ld_csr<NC>(&p.col_ptr[c + 1]);
                 while (pos < end) {  // 4 rows per step, their matches in flight together
                     int r[4], m[4];
 #pragma unroll
@@ -1280,6 +1293,34 @@ __device__ __forceinline__ void block_greedy_rounds(const Params& p, Smem& sm) {
                 }
             }
             __stcg(&p.root[c], want);
+        }
+        for (int k = warp; k < nlong; k += nwarps) {  // long lists: a warp each (warp-uniform)
+            const int c = __ldcg(&longs[k]);
+            if (!idx_ok(p, c, nc)) continue;
+            int want = -1;
+            if (__ldcg(&p.cmatch[c]) == -1) {
+                const int end = ld_csr<NC>(&p.col_ptr[c + 1]);
+                int pos = __ldcg(&p.level[c]);
+                while (pos < end) {
+                    const int r = pos + lane < end ? ld_csr<NC>(&p.row_idx[pos + lane]) : -1;
+                    const int m = (r >= 0 && idx_ok(p, r, p.nr)) ? __ldcg(&p.rmatch[r]) : 0;
+                    const unsigned free_rows = __ballot_sync(FULL, r >= 0 && m == -1);
+                    if (free_rows) {
+                        const int k0 = __ffs(free_rows) - 1;
+                        pos += k0;
+                        want = __shfl_sync(FULL, r, k0);
+                        break;
+                    }
+                    pos += 32;
+                }
+                if (pos > end) pos = end;
+                if (lane == 0) {
+                    __stcg(&p.level[c], pos);
+                    if (want >= 0) atomicMin(&p.ekey[want], (unsigned long long)(unsigned)c);
+                }
+                if (want >= 0) any = true;
+            }
+            if (lane == 0) __stcg(&p.root[c], want);
         }
         if (any) sm.ok = 1;
         __syncthreads();

@@ -346,7 +346,7 @@ void launch_workers(bm_server* s) {
 // A request large enough to run alone on the whole GPU (the persistent
 // single-graph kernel) rather than on one worker block.
 bool is_exclusive(const bm_server* s, const Request& r) {
-    return !s->opt.deterministic && s->opt.exclusive_min_edges > 0 && r.nnz >= s->opt.exclusive_min_edges;
+    return s->opt.exclusive_min_edges > 0 && r.nnz >= s->opt.exclusive_min_edges;
 }
 
 // Starts request r alone on the whole GPU: the workers are told to leave, and
@@ -354,7 +354,7 @@ bool is_exclusive(const bm_server* s, const Request& r) {
 // the copy of its control block and an event.  Returns BM_OK or an error.
 int32_t start_exclusive(bm_server* s, Request& r, int slot) {
     size_t offs[kOffs];
-    request_bytes(r.nr, r.nc, r.nnz, true, false, offs);
+    request_bytes(r.nr, r.nc, r.nnz, true, s->opt.deterministic != 0, offs);
     unsigned char* b = s->pool + r.off;
     bmd::Params p{};
     p.nr = r.nr;
@@ -372,6 +372,11 @@ int32_t start_exclusive(bm_server* s, Request& r, int slot) {
     p.rvis = (int32_t*)(b + offs[10]);
     p.crec = (int2*)(b + offs[11]);
     p.ctl = (bmd::Ctl*)(b + offs[12]);
+    if (s->opt.deterministic) {  // the same rules as the workers: the same result on either lane
+        p.dkey = (unsigned long long*)(b + offs[13]);
+        p.ekey = (unsigned long long*)(b + offs[14]);
+        p.ecand = (int32_t*)(b + offs[15]);
+    }
     p.mode = s->opt.mode;
     p.one_ep = 1;
     // alongside: the launch takes one block per SM beside the workers' one, on its own
@@ -593,7 +598,7 @@ int32_t bm_server_create(const bm_server_options* opt, bm_server** out) {
     if (per_sm < 1) return fail(BM_ERR_UNSUPPORTED);
     s->block = o.block_size;
     // alongside: one worker block per SM, leaving the other half of each SM to the whole-GPU lane
-    const int bps = (o.exclusive_alongside && !o.deterministic) ? 1 : (o.blocks_per_sm < per_sm ? o.blocks_per_sm : per_sm);
+    const int bps = o.exclusive_alongside ? 1 : (o.blocks_per_sm < per_sm ? o.blocks_per_sm : per_sm);
     s->grid = s->num_sms * bps;
     size_t pool = (size_t)o.pool_bytes;
     if (pool == 0) {

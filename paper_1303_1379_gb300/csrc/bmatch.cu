@@ -473,28 +473,44 @@ void launch_greedy(int nc, const int32_t* cp, const int32_t* ri, int32_t* rm, in
 // cooperative launch): rounds in which every unmatched column proposes to the
 // first unmatched row of its list and every proposed row takes the smallest
 // proposing column (atomicMin in ekey[r]), until a round without proposals.
-// Scratch: level (per column: position in its list), root (per column: the
-// row proposed to, -1 none); ekey is all ones before and after.  A column is
-// always handled by the same thread, so its scratch needs no barrier.
+// Columns of more than 32 rows look for their row a warp at a time, 32 rows
+// per step (a ballot of the free ones), from a list built at the start in the
+// queue buffer; the others a thread each.  Scratch: level (per column:
+// position in its list), root (per column: the row proposed to, -1 none);
+// ekey is all ones before and after.
 __global__ void __launch_bounds__(1024, 1) k_greedy_rounds(Params p) {
     using namespace bmd;
     __shared__ Smem sm;
     if (threadIdx.x == 0) { sm.qn = 0; sm.npush = 0; sm.has_ep = 0; }
+    __syncthreads();
     int bid = 0;
     const unsigned long long deadline = globaltimer() + (unsigned long long)p.total_ns;
     if (ld_volatile(&p.ctl->err) != 0) return;  // CSR check failed before launch
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthr = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const int warp = tid >> 5, nwarps = nthr >> 5;
     int32_t* pos = p.level;
     int32_t* want = p.root;
-    for (int c = tid; c < p.nc; c += nthr) __stcg(&pos[c], __ldg(&p.col_ptr[c]));
+    int32_t* longs = (int32_t*)p.queue;
+    for (int c = tid; c < p.nc; c += nthr) {
+        const int b = __ldg(&p.col_ptr[c]);
+        __stcg(&pos[c], b);
+        if (__ldg(&p.col_ptr[c + 1]) - b > 32) {
+            push(longs, 0, &p.ctl->qcnt[0], c);
+            atomicAdd(&sm.npush, 1);
+        }
+    }
+    if (!grid_sync(p.ctl, bid, p.wait_ns, deadline, sm, nullptr)) return;
+    const int nlong = sm.bc_a;
     for (int round = 0; round <= p.nc; ++round) {
         bool any = false;
-        for (int c = tid; c < p.nc; c += nthr) {
+        for (int c = tid; c < p.nc; c += nthr) {  // short lists: a thread each
+            const int end = __ldg(&p.col_ptr[c + 1]);
+            int at = __ldcg(&pos[c]);
+            if (end - __ldg(&p.col_ptr[c]) > 32) continue;
             int w = -1;
             if (__ldcg(&p.cmatch[c]) == -1) {
-                int at = __ldcg(&pos[c]);
-                const int end = __ldg(&p.col_ptr[c + 1]);
                 while (at < end) {  // 4 rows per step, their matches in flight together
                     int r[4], m[4];
 #pragma unroll
@@ -514,6 +530,34 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_rounds(Params p) {
                 }
             }
             __stcg(&want[c], w);
+        }
+        for (int k = warp; k < nlong; k += nwarps) {  // long lists: a warp each (warp-uniform)
+            const int c = __ldcg(&longs[k]);
+            if (!idx_ok(p, c, p.nc)) continue;
+            int w = -1;
+            if (__ldcg(&p.cmatch[c]) == -1) {
+                const int end = __ldg(&p.col_ptr[c + 1]);
+                int at = __ldcg(&pos[c]);
+                while (at < end) {
+                    const int r = at + lane < end ? __ldg(&p.row_idx[at + lane]) : -1;
+                    const int m = (r >= 0 && idx_ok(p, r, p.nr)) ? __ldcg(&p.rmatch[r]) : 0;
+                    const unsigned free_rows = __ballot_sync(FULL, r >= 0 && m == -1);
+                    if (free_rows) {
+                        const int k0 = __ffs(free_rows) - 1;
+                        at += k0;
+                        w = __shfl_sync(FULL, r, k0);
+                        break;
+                    }
+                    at += 32;
+                }
+                if (at > end) at = end;
+                if (lane == 0) {
+                    __stcg(&pos[c], at);
+                    if (w >= 0) atomicMin(&p.ekey[w], (unsigned long long)(unsigned)c);
+                }
+                if (w >= 0) any = true;
+            }
+            if (lane == 0) __stcg(&want[c], w);
         }
         if (any) sm.has_ep = 1;
         if (!grid_sync(p.ctl, bid, p.wait_ns, deadline, sm, nullptr)) return;
@@ -1423,7 +1467,7 @@ extern "C" int32_t bm_match_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
 namespace {
 struct ExclusiveDevice {
     bool ready;
-    int grid[2];  // cooperative grid of k_match<false, true>, k_match<true, true>
+    int grid[4];  // cooperative grid of k_match<false, true>, <true, true>, <true, true, true>; k_greedy_rounds
     int sms;
 };
 ExclusiveDevice g_excl_dev[kMaxDevices];
@@ -1446,11 +1490,13 @@ int32_t bmi::enqueue_match(bmd::Params p, long long nnz, bool wr, int greedy, cu
                 return BM_ERR_CUDA;
             }
             if (!coop) return BM_ERR_UNSUPPORTED;
-            for (int w = 0; w < 2; ++w) {
+            for (int w = 0; w < 4; ++w) {
                 int per_sm = 0;
                 const cudaError_t r =
-                    w ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true, true>, kDefaultBlock, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<false, true>, kDefaultBlock, 0);
+                    w == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy_rounds, kDefaultBlock, 0)
+                    : w == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true, true, true>, kDefaultBlock, 0)
+                    : w ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<true, true>, kDefaultBlock, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<false, true>, kDefaultBlock, 0);
                 if (r != cudaSuccess) { (void)cudaGetLastError(); return BM_ERR_CUDA; }
                 if (per_sm > 2048 / kDefaultBlock) per_sm = 2048 / kDefaultBlock;
                 while (per_sm > 1 && per_sm * sms > 2047) --per_sm;  // barrier words count blocks in 11 bits
@@ -1479,7 +1525,26 @@ int32_t bmi::enqueue_match(bmd::Params p, long long nnz, bool wr, int greedy, cu
         (void)cudaGetLastError();
         return BM_ERR_CUDA;
     }
-    if (greedy) {
+    const bool det = p.dkey != nullptr;  // deterministic option (GPUBFS-WR, one endpoint per root)
+    auto cap = [&](int g) { return (blocks_per_sm > 0 && g > blocks_per_sm * d.sms) ? blocks_per_sm * d.sms : g; };
+    if (det && ((nc && cudaMemsetAsync(p.dkey, 0xff, 8 * nc, st) != cudaSuccess) ||
+                (nr && cudaMemsetAsync(p.ekey, 0xff, 8 * nr, st) != cudaSuccess))) {
+        (void)cudaGetLastError();
+        return BM_ERR_CUDA;
+    }
+    if (greedy && det) {
+        // proposal rounds; their barrier words and list count are cleared for the matching
+        // kernel afterwards (the error word, set by the CSR check, stays)
+        if (p.wait_ns <= 0) p.wait_ns = 5000000000LL;
+        if (p.total_ns <= 0) p.total_ns = 120000000000LL;
+        void* gargs[] = {&p};
+        if (cudaLaunchCooperativeKernel((const void*)k_greedy_rounds, cap(d.grid[3]), B, gargs, 0, st) != cudaSuccess ||
+            cudaMemsetAsync(&p.ctl->arrive[0][0], 0, sizeof(p.ctl->arrive), st) != cudaSuccess ||
+            cudaMemsetAsync(&p.ctl->qcnt[0], 0, 2 * sizeof(int32_t), st) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return BM_ERR_CUDA;
+        }
+    } else if (greedy) {
         // the cheap matching counts its lists in the control block's first two queue
         // counters, which the matching kernel needs at zero
         launch_greedy(p.nc, p.col_ptr, p.row_idx, p.rmatch, p.cmatch, p.ctl, (int32_t*)p.queue, &p.ctl->qcnt[0],
@@ -1500,10 +1565,10 @@ int32_t bmi::enqueue_match(bmd::Params p, long long nnz, bool wr, int greedy, cu
     if (p.wait_ns <= 0) p.wait_ns = 5000000000LL;
     if (p.total_ns <= 0) p.total_ns = 120000000000LL;
     void* args[] = {&p};
-    int grid = d.grid[wr ? 1 : 0];
-    if (blocks_per_sm > 0 && grid > blocks_per_sm * d.sms) grid = blocks_per_sm * d.sms;
-    const cudaError_t e = wr ? cudaLaunchCooperativeKernel((const void*)k_match<true, true>, grid, B, args, 0, st)
-                             : cudaLaunchCooperativeKernel((const void*)k_match<false, true>, grid, B, args, 0, st);
+    const int grid = cap(d.grid[det ? 2 : wr ? 1 : 0]);
+    const cudaError_t e = det  ? cudaLaunchCooperativeKernel((const void*)k_match<true, true, true>, grid, B, args, 0, st)
+                          : wr ? cudaLaunchCooperativeKernel((const void*)k_match<true, true>, grid, B, args, 0, st)
+                               : cudaLaunchCooperativeKernel((const void*)k_match<false, true>, grid, B, args, 0, st);
     if (e != cudaSuccess) { (void)cudaGetLastError(); return BM_ERR_CUDA; }
     return BM_OK;
 }

@@ -184,9 +184,9 @@ def test_batch_same_for_every_geometry(block, per_sm):
 
 # ------------------------------------------------------------ served path
 def served_requests():
-    """Uniform and R-MAT requests of 50 to 20,000 rows, and one R-MAT request
-    of about 700 k edges (above the default threshold for the single-graph
-    lane; with the option every request runs on a worker block)."""
+    """Uniform and R-MAT requests of 50 to 20,000 rows (worker blocks), and one
+    R-MAT request of about 700 k edges (above the default threshold: the
+    single-graph kernel, beside the workers)."""
     rng = np.random.default_rng(77)
     out = []
     for i in range(24):
@@ -234,7 +234,7 @@ def test_served_results_equal_the_oracle_alone_and_in_the_mix():
             np.testing.assert_array_equal(rm, w[0])
             np.testing.assert_array_equal(cm, w[1])
         st = srv.stats()
-        assert st["exclusive_runs"] == 0 and st["pool_used"] == 0
+        assert st["exclusive_runs"] == 2 and st["pool_used"] == 0  # the large request, alone and in the mix
 
 
 # ------------------------------------------------------------ cheap matching in rounds
