@@ -72,6 +72,8 @@ def parse():
                     help="threads x blocks per SM of the batched launch (e.g. 512x2) instead of the "
                          "autotuner's choice (profiling captures)")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-det", action="store_true",
+                    help="skip the deterministic option's leg on the single-graph workloads")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-distinct", type=int, default=48)
     ap.add_argument("--serve-one-by-one", type=int, default=2000,
@@ -279,17 +281,23 @@ def load_workload(name):
     return synth.workload(name)
 
 
-def golden_max(name):
-    name = name[:-4] if name.endswith("-rcp") else name  # permutation keeps |M|
+def golden_fields(name):
+    """The stored line of tests/golden/workloads.txt for a workload (written by
+    tests/golden/make_golden.py from the oracle alone), as a dict, or None."""
     try:
         with open(os.path.join(ROOT, "tests", "golden", "workloads.txt")) as f:
             for line in f:
                 t = line.split("#")[0].split()
                 if t and t[0] == name:
-                    return int(dict(kv.split("=") for kv in t[1:])["max"])
+                    return dict(kv.split("=") for kv in t[1:])
     except Exception:
         pass
     return None
+
+
+def golden_max(name):
+    f = golden_fields(name[:-4] if name.endswith("-rcp") else name)  # permutation keeps |M|
+    return int(f["max"]) if f else None
 
 
 # ------------------------------------------------------------------ reference arm
@@ -709,6 +717,37 @@ def bench_graph(name, args, torch, bmatch, stream, flush, dev, steps, warmup, wo
         ipm.append(a.elapsed_time(b))
     m.close()
 
+    # the deterministic option: proposal-round cheap matching + search from the empty
+    # matching; its row-to-column array is compared (SHA-256 prefix) with the oracle's
+    det = None
+    if not args.no_det:
+        dm = bmatch.Matcher(nr, nc, nnz, cp, ri, stream=stream.cuda_stream, deterministic=1)
+        rmd = torch.empty(max(nr, 1), dtype=torch.int32, device=dev)
+        d_ms, dres = [], None
+        for i in range(4):
+            flush.fill_(i)
+            dm.set_matching(None, None)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dm.greedy()
+            dres = dm.match(rmd)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i:
+                d_ms.append(a.elapsed_time(b))
+        dm.close()
+        sha = hashlib.sha256(rmd[:nr].cpu().numpy().astype("<i4").tobytes()).hexdigest()[:16]
+        gold = None if name.endswith("-rcp") else golden_fields(name)
+        det = {"init_plus_match_ms": statistics.median(d_ms), "max_matching": dres.card,
+               "phases": dres.stats["phases"], "levels": dres.stats["levels"], "rmatch_sha": sha,
+               "same_as_oracle": None if not gold or "det_rmatch_sha" not in gold else
+               bool(sha == gold["det_rmatch_sha"] and dres.stats["phases"] == int(gold["det_phases"])
+                    and dres.stats["levels"] == int(gold["det_levels"])),
+               "note": "bm_options.deterministic: cheap matching in proposal rounds, then the search "
+                       "with smallest-id tie-breaks, from the empty matching, median of 3; rmatch "
+                       "compared by SHA-256 with the oracle's (tests/golden/workloads.txt)"}
+
     # roofline of the dominant kernel (the persistent matching launch)
     peak, peak_kind = measured_peaks()
     st0 = stats[-1]
@@ -735,6 +774,8 @@ def bench_graph(name, args, torch, bmatch, stream, flush, dev, steps, warmup, wo
                                                      "edges_scanned", "edges_to_matched", "inserted",
                                                      "endpoints", "alternate_steps", "roots")}},
     }
+    if det is not None:
+        out["deterministic"] = det
     if e2e:
         hm = bmatch.Matcher(nr, nc, nnz, None, None, stream=stream.cuda_stream)
         h_cp = torch.from_numpy(g.col_ptr).pin_memory()
@@ -878,6 +919,7 @@ def run_ours(args):
         "roofline": main["roofline"],
         "cpu_baseline": cpu,
         "e2e": main.get("e2e"),
+        "deterministic": main.get("deterministic"),
         "workloads": workloads,
         "batched": batched,
         "served": served,
