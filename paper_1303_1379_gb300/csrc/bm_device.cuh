@@ -1366,6 +1366,7 @@ __device__ int block_match_graph_det(const Params& p, int greedy, Smem& sm, Coun
     for (int c = t; c < nc; c += T) __stcg(&p.dkey[c], DKEY_NONE);
     __syncthreads();
     if (greedy) block_greedy_rounds<NC>(p, sm);
+    if (t == 0) sm.ok = 0;  // the rounds used it as their flag; from here it holds Alternate's errors
     const int max_phases = (nr < nc ? nr : nc) + 2;
     int phases = 0, card = 0, status = 0;
     long long levels_total = 0, eps_total = 0, ins_total = 0;
