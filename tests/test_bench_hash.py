@@ -46,3 +46,14 @@ def test_source_hash_tracks_each_kernel():
     b = _bench()
     h1, h2 = b.source_hash("k_match"), b.source_hash("k_batch")
     assert len(h1) == len(h2) == 16 and h1 != h2
+
+
+def test_golden_lines_parse():
+    """Every stored workload line parses (numbers and the deterministic
+    option's array digest), as bench.py reads it."""
+    b = _bench()
+    for name in ("uniform10k", "rmat21", "stencil2000"):
+        f = b.golden_fields(name)
+        assert int(f["max"]) > 0 and int(f["det_phases"]) >= 1 and int(f["det_levels"]) >= 1
+        assert len(f["det_rmatch_sha"]) == 16
+        assert b.golden_max(name) == int(f["max"]) == b.golden_max(name + "-rcp")

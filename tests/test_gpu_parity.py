@@ -29,7 +29,8 @@ def golden_workloads():
         for line in f:
             line = line.split("#")[0].split()
             if line:
-                out[line[0]] = {k: int(v) for k, v in (kv.split("=") for kv in line[1:])}
+                out[line[0]] = {k: int(v) if v.lstrip("-").isdigit() else v
+                                for k, v in (kv.split("=") for kv in line[1:])}
     return out
 
 
