@@ -77,7 +77,10 @@ struct alignas(128) Ctl {
     int32_t n_endpoints_last;  // endpoints of the last BFS (inspection)
     int32_t searches;          // breadth-first searches run (entries of the phase profile)
     int32_t dcnt[3];           // deterministic option: rows listed in ecand during a step
-    int32_t pad1[7];
+    int32_t ep_alt;            // the persistent one-endpoint kernel's even phases count their endpoints
+                               // here (odd ones in ep_phase), so that each phase's counter can be
+                               // cleared during the phase before it
+    int32_t pad1[6];
     long long levels;
     long long max_levels;
     long long cols_expanded;
@@ -376,7 +379,13 @@ __device__ __forceinline__ void step_init(const Params& p, int2* q, int slot, Co
 // unmatched are appended to the other queue buffer as the next phase's roots.
 // DET (deterministic option): the inserted columns' tree-entry keys and the
 // roots' endpoint picks (the roots' own key words) go back to "none" too.
-template <bool WR, bool DET = false>
+// SERVED: a root counts as matched when its level slot says it took an
+// endpoint (-(row)), not by its cmatch entry -- the same set once Alternate
+// has walked every path to its root, and known before: this pass may then
+// run while the walks are still going (neither touches what the other reads
+// or writes: the walks use crec, pred, cmatch and rmatch; this pass the
+// queue, level, root and the keys).
+template <bool WR, bool DET = false, bool SERVED = false>
 __device__ __forceinline__ void step_next_roots(const Params& p, const int2* q, int n_roots, int tail,
                                                 int2* q_next, int slot, Smem& sm) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -404,7 +413,8 @@ __device__ __forceinline__ void step_next_roots(const Params& p, const int2* q, 
             if (c[u] >= 0 && !idx_ok(p, c[u], p.nc)) c[u] = -1;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) m[u] = c[u] >= 0 ? __ldcg(&p.cmatch[c[u]]) : 0;
+        for (int u = 0; u < 4; ++u)
+            m[u] = c[u] < 0 ? 0 : SERVED ? (__ldcg(&p.level[c[u]]) == L0 ? -1 : 0) : __ldcg(&p.cmatch[c[u]]);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (c[u] < 0) continue;
@@ -625,7 +635,7 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
 // from the step's tile counter.
 template <bool WR, bool RV = false, bool GRID = false>
 __device__ __forceinline__ void step_expand(const Params& p, int2* queue, int qb, int qe, int lvl, int slot,
-                                            Counters& cnt, Smem& sm, int stamp = 0) {
+                                            Counters& cnt, Smem& sm, int stamp = 0, int32_t* ep_ctr = nullptr) {
     const int q = qe - qb;
     // tile width: spread small frontiers over many blocks, never above blockDim
     int tw = (q + gridDim.x - 1) / gridDim.x;
@@ -635,7 +645,8 @@ __device__ __forceinline__ void step_expand(const Params& p, int2* queue, int qb
     const int ntiles = (q + tw - 1) / tw;
     const bool narrow = ntiles <= (int)gridDim.x;
     auto push_col = [&](int2 v) { push_block(p, queue, sm, qe, slot, v); };
-    auto push_end = [&](int v) { push(p.endpoints, 0, &p.ctl->ep_phase, v); };
+    int32_t* const epc = ep_ctr ? ep_ctr : &p.ctl->ep_phase;
+    auto push_end = [&](int v) { push(p.endpoints, 0, epc, v); };
     if (GRID && !narrow) {
         // Guided self-scheduling of a wide level: block b first takes columns
         // [b w0, (b + 1) w0) with w0 ~ q / 2G, then ranges from a position
@@ -876,9 +887,9 @@ __device__ __forceinline__ void det_take(const Params& p, int n, int i0, int str
 __device__ __forceinline__ void step_det_offer(const Params& p, int n) {
     det_offer(p, n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
-__device__ __forceinline__ void step_det_take(const Params& p, int n) {
+__device__ __forceinline__ void step_det_take(const Params& p, int n, int32_t* ep_ctr) {
     det_take(p, n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x,
-             [&](int r) { push(p.endpoints, 0, &p.ctl->ep_phase, r); });
+             [&](int r) { push(p.endpoints, 0, ep_ctr, r); });
 }
 
 // ------------------------------------------------------------------ Alternate

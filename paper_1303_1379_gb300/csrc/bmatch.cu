@@ -99,6 +99,9 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
             break;
         }
         ++phases;
+        // the phase's endpoint counter (incremental mode: two, alternating by phase,
+        // each cleared during the phase before it uses it)
+        int32_t* const epc = (incr && (phases & 1) == 0) ? &ctl->ep_alt : &ctl->ep_phase;
 
         // ---- BFS, level by level (Algorithm 1 inner loop)
         int qb = 0, qe = n_roots, lvl = L0, tail = n_roots;
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
                 if (DET) ctl->dcnt[(s2 + 1) % 3] = 0;
             }
             if constexpr (DET) step_expand_det(p, qcur, qb, qe, lvl, s2 % 3, cnt, sm);
-            else step_expand<WR, RV, true>(p, qcur, qb, qe, lvl, s2 % 3, cnt, sm, p.stamp_base + phases);
+            else step_expand<WR, RV, true>(p, qcur, qb, qe, lvl, s2 % 3, cnt, sm, p.stamp_base + phases, epc);
             if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, DET ? &ctl->dcnt[s2 % 3] : nullptr)) goto out;
             const int nq = sm.bc_a;           // columns inserted at this level
             const bool found = sm.bc_b > 0;   // some block claimed an endpoint (DET: received an offer)
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
                     const int n_off = sm.bc_c;
                     step_det_offer(p, n_off);
                     if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
-                    step_det_take(p, n_off);
+                    step_det_take(p, n_off, epc);
                     if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
                 }
             }
@@ -138,7 +141,7 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
             qe += nq;
             ++lvl;
         }
-        if (threadIdx.x == 0) sm.bc_c = ld_volatile(&ctl->ep_phase);  // all appends precede the barrier
+        if (threadIdx.x == 0) sm.bc_c = ld_volatile(epc);  // all appends precede the barrier
         __syncthreads();
         const int n_ep = sm.bc_c;
         if (leader) {
@@ -163,18 +166,31 @@ __global__ void __launch_bounds__(1024, 1) k_match(Params p) {
         if (n_ep == 0) break;  // no augmenting path: the matching is maximum (Berge)
 
         // ---- Alternate (Algorithm 3); the walk is at most as long as the forest
-        if (RV && incr) step_alternate_disjoint(p, n_ep, tail + 2);
-        else step_alternate(p, n_ep, tail + 2, cnt);
-        if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
-        if (incr) {
-            // ---- next phase's roots: the unmatched ones among this phase's roots
+        if (RV && incr) {
+            // disjoint walks, and with them the next phase's roots (the roots that took
+            // no endpoint), in one step: see step_next_roots
             const int s3 = step++;
             if (leader) {
                 ctl->qcnt[(s3 + 1) % 3] = 0; ctl->ecnt[(s3 + 1) % 3] = 0; ctl->icnt[(s3 + 1) % 3] = 0; ctl->tcnt[(s3 + 1) % 3] = 0;
                 if (DET) ctl->dcnt[(s3 + 1) % 3] = 0;
-                ctl->ep_phase = 0;
+                *(epc == &ctl->ep_phase ? &ctl->ep_alt : &ctl->ep_phase) = 0;  // the next phase's counter
             }
-            step_next_roots<WR, DET>(p, qcur, n_roots, tail, qnext, s3 % 3, sm);
+            step_alternate_disjoint(p, n_ep, tail + 2);
+            step_next_roots<WR, DET, true>(p, qcur, n_roots, tail, qnext, s3 % 3, sm);
+        } else {
+            step_alternate(p, n_ep, tail + 2, cnt);
+            if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
+            if (incr) {
+                const int s3 = step++;
+                if (leader) {
+                    ctl->qcnt[(s3 + 1) % 3] = 0; ctl->ecnt[(s3 + 1) % 3] = 0; ctl->icnt[(s3 + 1) % 3] = 0; ctl->tcnt[(s3 + 1) % 3] = 0;
+                    *(epc == &ctl->ep_phase ? &ctl->ep_alt : &ctl->ep_phase) = 0;  // the next phase's counter
+                }
+                step_next_roots<WR>(p, qcur, n_roots, tail, qnext, s3 % 3, sm);
+            }
+        }
+        if (incr) {
+            // ---- next phase's roots: the unmatched ones among this phase's roots
             if (!grid_sync(ctl, bid, p.wait_ns, deadline, sm, nullptr)) goto out;
             n_roots = sm.bc_a;
 #ifdef BM_CHECKED
