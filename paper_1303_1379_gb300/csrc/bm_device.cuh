@@ -340,23 +340,37 @@ __device__ __forceinline__ void step_init(const Params& p, int2* q, int slot, Co
     const int nc = p.nc;
     int nfree = 0, niso = 0;
     unsigned fixes = 0;
-    for (int base = blockIdx.x * blockDim.x; base < nc; base += gridDim.x * blockDim.x) {  // block-uniform
-        const int c = base + threadIdx.x;
-        if (c < nc) {
-            int r = __ldcg(&p.cmatch[c]);
-            if (r >= 0 && !idx_ok(p, r, p.nr)) r = -1;
-            if (r >= 0 && __ldcg(&p.rmatch[r]) != c) {
-                __stcg(&p.cmatch[c], -1);
-                r = -1;
+    // 4 columns per thread per pass, their loads in flight together (a pass appends at
+    // most 4 x blockDim <= QBUF entries per block)
+    const int T = blockDim.x;
+    for (int base = blockIdx.x * 4 * T; base < nc; base += gridDim.x * 4 * T) {  // block-uniform
+        int c[4], r[4], back[4], deg[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            c[u] = base + u * T + threadIdx.x;
+            r[u] = c[u] < nc ? __ldcg(&p.cmatch[c[u]]) : -2;
+            if (r[u] >= 0 && !idx_ok(p, r[u], p.nr)) r[u] = -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            back[u] = r[u] >= 0 ? __ldcg(&p.rmatch[r[u]]) : -1;
+            deg[u] = c[u] < nc ? __ldg(&p.col_ptr[c[u] + 1]) - __ldg(&p.col_ptr[c[u]]) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (c[u] >= nc) continue;
+            if (r[u] >= 0 && back[u] != c[u]) {
+                __stcg(&p.cmatch[c[u]], -1);
+                r[u] = -1;
                 ++fixes;
             }
-            const bool is_free = (r < 0);
-            __stcg(&p.level[c], is_free ? L0 : L0 - 1);
-            if (WR) __stcg(&p.root[c], is_free ? c : -1);
+            const bool is_free = (r[u] < 0);
+            __stcg(&p.level[c[u]], is_free ? L0 : L0 - 1);
+            if (WR) __stcg(&p.root[c[u]], is_free ? c[u] : -1);
             if (is_free) {
-                if (p.crec) __stcg(&p.crec[c], make_int2(-1, -1));
+                if (p.crec) __stcg(&p.crec[c[u]], make_int2(-1, -1));
                 ++nfree;
-                if (__ldg(&p.col_ptr[c + 1]) > __ldg(&p.col_ptr[c])) push_block(p, q, sm, 0, slot, make_int2(c, c));
+                if (deg[u] > 0) push_block(p, q, sm, 0, slot, make_int2(c[u], c[u]));
                 else ++niso;
             }
         }
