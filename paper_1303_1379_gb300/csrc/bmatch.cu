@@ -306,6 +306,48 @@ __global__ void k_check_matching(int nr, int nc, const int32_t* __restrict__ rm,
     if (bad) bmd::set_error(ctl, BM_ERR_INVALID_MATCHING);
 }
 
+// Installs a matching (rm0/cm0 -> rm/cm) and checks it on the way: every
+// entry in range, rm0 and cm0 inverse to each other (BM_ERR_INVALID_MATCHING
+// in ctl->err otherwise).  4 entries per thread per pass, their loads in
+// flight together; the checks read the source arrays, so nothing waits for
+// the copies.
+__global__ void k_install_matching(int nr, int nc, const int32_t* __restrict__ rm0,
+                                   const int32_t* __restrict__ cm0, int32_t* __restrict__ rm,
+                                   int32_t* __restrict__ cm, Ctl* ctl) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthr = gridDim.x * blockDim.x;
+    bool bad = false;
+    for (int r0 = tid; r0 < nr; r0 += 4 * nthr) {
+        int c[4], back[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = r0 + u * nthr < nr ? __ldg(&rm0[r0 + u * nthr]) : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) back[u] = (c[u] >= 0 && c[u] < nc) ? __ldg(&cm0[c[u]]) : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = r0 + u * nthr;
+            if (r >= nr) continue;
+            rm[r] = c[u];
+            if (c[u] != -1 && (c[u] < 0 || c[u] >= nc || back[u] != r)) bad = true;
+        }
+    }
+    for (int c0 = tid; c0 < nc; c0 += 4 * nthr) {
+        int r[4], back[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) r[u] = c0 + u * nthr < nc ? __ldg(&cm0[c0 + u * nthr]) : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) back[u] = (r[u] >= 0 && r[u] < nr) ? __ldg(&rm0[r[u]]) : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u * nthr;
+            if (c >= nc) continue;
+            cm[c] = r[u];
+            if (r[u] != -1 && (r[u] < 0 || r[u] >= nr || back[u] != c)) bad = true;
+        }
+    }
+    if (bad) bmd::set_error(ctl, BM_ERR_INVALID_MATCHING);
+}
+
 __global__ void k_fill(int32_t* a, long long n, int v) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
@@ -1208,11 +1250,10 @@ int32_t bm_match_from(bm_ctx* ctx, const int32_t* rmatch0, const int32_t* cmatch
     if (ctx->sticky || !ctx->csr_ready) return BM_ERR_STATE;
     cudaStream_t st = ctx->stream;
     BM_CUDA(ctx, cudaMemsetAsync(ctx->ctl, 0, sizeof(Ctl), st));
-    if (ctx->nr) BM_CUDA(ctx, cudaMemcpyAsync(ctx->rmatch, rmatch0, 4 * (size_t)ctx->nr, cudaMemcpyDeviceToDevice, st));
-    if (ctx->nc) BM_CUDA(ctx, cudaMemcpyAsync(ctx->cmatch, cmatch0, 4 * (size_t)ctx->nc, cudaMemcpyDeviceToDevice, st));
-    // the check reports through the control block; the match launch then returns at once
-    k_check_matching<<<grid_for(ctx, ctx->nr > ctx->nc ? ctx->nr : ctx->nc), ctx->block, 0, st>>>(
-        ctx->nr, ctx->nc, ctx->rmatch, ctx->cmatch, ctx->ctl);
+    // copy and check in one launch; the check reports through the control block, and the
+    // match launch then returns at once
+    k_install_matching<<<grid_for(ctx, ((ctx->nr > ctx->nc ? ctx->nr : ctx->nc) + 3) / 4), ctx->block, 0, st>>>(
+        ctx->nr, ctx->nc, rmatch0, cmatch0, ctx->rmatch, ctx->cmatch, ctx->ctl);
     BM_CUDA(ctx, cudaGetLastError());
     int32_t rc = run(ctx, false);
     if (rc < 0) return rc;
