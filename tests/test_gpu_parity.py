@@ -379,12 +379,24 @@ def test_match_from_equals_set_matching_then_match():
             assert a.card == b.card == want
             assert b.stats["initial_card"] == int((cm0 >= 0).sum())
             assert_maximum(g, rm.cpu().numpy(), cm.cpu().numpy(), b.card, want)
-        bad = rm0.copy()
-        bad[int(np.flatnonzero(rm0 >= 0)[0])] = -1  # one row forgets its column
+        r_m = int(np.flatnonzero(rm0 >= 0)[0])
+        c_m = int(np.flatnonzero(cm0 >= 0)[0])
+        c_free = int(np.flatnonzero(cm0 < 0)[0])
+        bad_starts = []
+        b = rm0.copy(); b[r_m] = -1; bad_starts.append((b, cm0))            # a row forgets its column
+        b = cm0.copy(); b[c_free] = g.n_rows + 5; bad_starts.append((rm0, b))  # a column out of range
+        b = rm0.copy(); b[r_m] = -3; bad_starts.append((b, cm0))            # a negative code
+        b = cm0.copy(); b[c_free] = int(cm0[c_m]); bad_starts.append((rm0, b))  # two columns, one row
+        for brm, bcm in bad_starts:
+            with pytest.raises(bmatch.BMError) as e:
+                m.match_from(torch.from_numpy(brm).cuda(), torch.from_numpy(bcm).cuda())
+            assert e.value.status == bmatch.BM_ERR_INVALID_MATCHING
+            assert m.match_from(d_rm0, d_cm0).card == want  # the context is still usable
+    with bmatch.Matcher(g.n_rows, g.n_cols, g.nnz, cp, ri, driver=1) as h:  # the host loop's install path
+        assert h.match_from(d_rm0, d_cm0).card == want
         with pytest.raises(bmatch.BMError) as e:
-            m.match_from(torch.from_numpy(bad).cuda(), d_cm0)
+            h.match_from(torch.from_numpy(bad_starts[0][0]).cuda(), d_cm0)
         assert e.value.status == bmatch.BM_ERR_INVALID_MATCHING
-        assert m.match_from(d_rm0, d_cm0).card == want  # the context is still usable
 
 
 def test_phase_limit_gives_valid_partial_matchings(c1):
