@@ -273,3 +273,30 @@ def test_full_size_cheap_matching_in_rounds():
         rm = torch.empty(g.n_rows, dtype=torch.int32, device="cuda")
         m.get_matching(rm, None)
         np.testing.assert_array_equal(rm.cpu().numpy(), w_rm)
+
+
+def test_batch_apsb_same_as_the_oracle():
+    b = synth.batch_graphs(40, seed=43, nr_lo=10, nr_hi=3000)
+    R, C = int(b.row_off[-1]), int(b.col_off[-1])
+    w_rm = np.full(R, -1, np.int32)
+    for k in range(b.n_graphs):
+        g = b.graph(k)
+        rm0, cm0, _, _ = oracle.greedy_rounds(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+        rm, _, _, _ = oracle.apfb_wr_det(g.n_rows, g.n_cols, g.col_ptr, g.row_idx, rm0, cm0, apsb=True)
+        w_rm[b.row_off[k]:b.row_off[k + 1]] = rm
+    rm, _, _ = run_batch_det(b, True, mode=1)
+    np.testing.assert_array_equal(rm, w_rm)
+
+
+def test_match_host_buffers_deterministic():
+    # bm_match_host (host CSR and start, copies inside the call) under the option
+    from paper_1303_1379_gb300 import bmatch
+    g = graph("rmat15")
+    rm0, cm0 = start(g, "greedy")
+    w_rm, w_cm, w_card, _ = oracle.apfb_wr_det(g.n_rows, g.n_cols, g.col_ptr, g.row_idx, rm0, cm0)
+    with bmatch.Matcher(g.n_rows, g.n_cols, g.nnz, None, None, deterministic=1) as m:
+        h_rm, h_cm = rm0.copy(), cm0.copy()
+        res = m.match_host(g.col_ptr, g.row_idx, h_rm, h_cm)
+        assert res.card == w_card
+        np.testing.assert_array_equal(h_rm, w_rm)
+        np.testing.assert_array_equal(h_cm, w_cm)
