@@ -104,10 +104,14 @@ typedef struct bm_options {
                               and bm_greedy runs the cheap matching in rounds: every
                               unmatched column proposes to the first unmatched row of its
                               list, every proposed row takes the smallest proposing column,
-                              until no column proposes.  Needs the persistent driver, GPUBFS-WR and
-                              wr_one_endpoint = 1 (BM_ERR_INVALID_ARG otherwise); the
-                              context allocates 8*n_cols + 12*n_rows bytes on its first
-                              deterministic call (BM_ERR_NOMEM if that fails).  0 = default */
+                              until no column proposes.  Batches (bm_batch_create,
+                              bm_batch_set_options) follow the same rules graph by graph
+                              (their cheap matching too), for every launch geometry.  Needs
+                              GPUBFS-WR, wr_one_endpoint = 1 and, for a context, the
+                              persistent driver (BM_ERR_INVALID_ARG otherwise); a context
+                              allocates 8*n_cols + 12*n_rows bytes on its first deterministic
+                              call, a batch the same over all its graphs (BM_ERR_NOMEM if
+                              that fails).  0 = default                                    */
     int64_t wait_timeout_ns;  /* limit of one device-side barrier wait; 0 = 5 s             */
     int64_t total_timeout_ns; /* limit of one match launch; 0 = 120 s                       */
     int64_t reserved[6];
