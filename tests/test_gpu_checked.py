@@ -5,8 +5,9 @@ compute from data -- row ids, matched columns, roots, queue entries,
 predecessors -- before using it, and between phases checks that rmatch and
 cmatch are mutual inverses; a violation returns BM_ERR_CHECK.  It stands in
 for a memory checker (compute-sanitizer is closed on this machine).  These tests
-run the parity workloads of every variant, the batched path and the
-allocation-free entry point through it, in a fresh process (the library is
+run the parity workloads of every variant (the deterministic option too, whose
+matching must be the oracle's), the batched path and the allocation-free entry
+point through it, in a fresh process (the library is
 chosen at the first load), and require the oracle's |M| with no check firing.
 """
 import json
@@ -43,6 +44,11 @@ for name, g in graphs.items():
         rm, cm, card, st = gpu_match(g, (rm0, cm0), **v)
         assert_maximum(g, rm, cm, card, want)
         out.append([name, v, card, st["status"]])
+    for apsb in (0, 1):  # the deterministic option: the oracle's exact matching
+        w_rm, w_cm, _, _ = oracle.apfb_wr_det(g.n_rows, g.n_cols, g.col_ptr, g.row_idx, rm0, cm0, apsb=bool(apsb))
+        rm, cm, card, st = gpu_match(g, (rm0, cm0), deterministic=1, mode=apsb)
+        assert np.array_equal(rm, w_rm) and np.array_equal(cm, w_cm)
+        out.append([name, {"deterministic": 1, "mode": apsb}, card, st["status"]])
 # batched path
 b = synth.batch_graphs(64, seed=3)
 bb = bmatch.Batch.from_synth(b)
@@ -54,6 +60,16 @@ rc, st = bb.match(rm, cm, greedy=True, card_out=card)
 _, _, want = oracle.hk_batch(b, greedy_first=True)
 assert rc == 0 and np.array_equal(card.cpu().numpy(), want)
 out.append(["batch64", None, int(card.sum()), st["status"]])
+bd = bmatch.Batch.from_synth(b, deterministic=1)
+rm.fill_(-1); cm.fill_(-1)
+rc, st = bd.match(rm, cm, greedy=True)
+w_rm = np.full(R, -1, np.int32)
+for k in range(b.n_graphs):
+    gk = b.graph(k)
+    g_rm, g_cm, _, _ = oracle.greedy_rounds(gk.n_rows, gk.n_cols, gk.col_ptr, gk.row_idx)
+    w_rm[b.row_off[k]:b.row_off[k + 1]] = oracle.apfb_wr_det(gk.n_rows, gk.n_cols, gk.col_ptr, gk.row_idx, g_rm, g_cm)[0]
+assert rc == 0 and np.array_equal(rm.cpu().numpy(), w_rm)
+out.append(["batch64-deterministic", None, int((cm >= 0).sum()), st["status"]])
 # allocation-free entry point
 g = graphs["rmat15"]
 cp = torch.from_numpy(g.col_ptr).cuda(); ri = torch.from_numpy(g.row_idx).cuda()
@@ -75,5 +91,5 @@ def test_checked_build_runs_every_variant_without_a_check_firing():
     assert res.returncode == 0, res.stdout[-3000:] + res.stderr[-3000:]
     line = [l for l in res.stdout.splitlines() if l.startswith("RESULT ")][-1]
     rows = json.loads(line[7:])
-    assert len(rows) == 4 * 8 + 2
+    assert len(rows) == 4 * (8 + 2) + 3
     assert all(r[3] == 0 for r in rows)
