@@ -70,6 +70,7 @@ struct BatchParams {
 template <bool WR, bool DET = false>
 __global__ void __launch_bounds__(1024, 1) k_batch(BatchParams bp) {
     __shared__ Smem sm;
+    __shared__ unsigned s_vis[bmd::SB_MAX_COLS / 32], s_srv[bmd::SB_MAX_COLS / 32];  // see block_match_graph
     Counters cnt{0, 0, 0, 0, 0};
     long long lv_all = 0, ep_all = 0, ph_all = 0, ins_all = 0;
     for (;;) {
@@ -102,6 +103,10 @@ __global__ void __launch_bounds__(1024, 1) k_batch(BatchParams bp) {
             p.ekey = bp.ekey + ro;
             p.ecand = bp.ecand + ro;
             st = bmd::block_match_graph_det<true>(p, bp.greedy, sm, cnt, card, phases, levels, eps, ins);
+        } else if (WR && bp.one_ep && p.nc <= bmd::SB_MAX_COLS) {  // tree marks in shared memory
+            p.vis = s_vis;
+            p.srv = s_srv;
+            st = bmd::block_match_graph<WR, true, true, WR>(p, bp.greedy, sm, cnt, card, phases, levels, eps, ins);
         } else {
             st = bmd::block_match_graph<WR, true, true>(p, bp.greedy, sm, cnt, card, phases, levels, eps, ins);
         }

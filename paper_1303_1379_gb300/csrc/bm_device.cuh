@@ -126,6 +126,11 @@ struct Params {
     unsigned long long* dkey;
     unsigned long long* ekey;
     int32_t* ecand;
+    // one block per graph, one endpoint per root (SB instantiations): bitmaps in shared
+    // memory of the columns already in a tree and of the roots already served, in place of
+    // the level array's tests and claims
+    unsigned* vis;
+    unsigned* srv;
 };
 
 // Per-block shared state of the steps.
@@ -189,6 +194,17 @@ template <bool NC>
 __device__ __forceinline__ int ld_csr(const int32_t* p) {
     if (NC) return __ldg(p);
     return __ldcg(p);
+}
+
+// Shared-memory bitmaps of the one-block-per-graph routine (p.vis, p.srv).
+constexpr int SB_MAX_COLS = 65536;  // columns a graph may have for the bitmaps (8 KB each)
+__device__ __forceinline__ bool sb_test(const unsigned* b, int i) {
+    return (((const volatile unsigned*)b)[i >> 5] >> (i & 31)) & 1u;
+}
+// Sets bit i; true if this call set it (it was clear).
+__device__ __forceinline__ bool sb_claim(unsigned* b, int i) {
+    const unsigned m = 1u << (i & 31);
+    return !(atomicOr(&b[i >> 5], m) & m);
 }
 
 // Appends v at base + (running count of `slot`) with one atomic per group of
@@ -457,7 +473,7 @@ __device__ __forceinline__ void step_next_roots(const Params& p, const int2* q, 
 // old value, after adding `grab` (a tile index with grab 1 and ctr_base
 // gridDim.x; a queue position with a range width and the end of the static
 // ranges in the guided schedule).  Ends with __syncthreads.
-template <bool WR, bool NC = true>
+template <bool WR, bool NC = true, bool SB = false>
 __device__ __forceinline__ void tile_load(const Params& p, const int2* queue, int qb, int q, int first, int tw,
                                           Smem& sm, Counters& cnt, int32_t* tile_ctr, int grab = 1, int ctr_base = -1) {
     const int t = threadIdx.x;
@@ -472,7 +488,7 @@ __device__ __forceinline__ void tile_load(const Params& p, const int2* queue, in
         } else {
             beg = ld_csr<NC>(&p.col_ptr[c]);
             deg = ld_csr<NC>(&p.col_ptr[c + 1]) - beg;
-            if (WR) rlev = __ldcg(&p.level[myroot]);
+            if (WR) rlev = SB ? (sb_test(p.srv, myroot) ? L0 - 2 : L0) : __ldcg(&p.level[myroot]);
         }
     }
     if (t == 0 && tile_ctr) sm.tile = (ctr_base < 0 ? (int)gridDim.x : ctr_base) + atomicAdd(tile_ctr, grab);
@@ -490,7 +506,7 @@ __device__ __forceinline__ void tile_load(const Params& p, const int2* queue, in
 // <= MAX_BLOCK): the one-block-per-graph routine, where a level's tiles run
 // one after another in one block, gets twice the columns (and their loads)
 // in flight per tile.  Ends with __syncthreads.
-template <bool WR, bool NC = true>
+template <bool WR, bool NC = true, bool SB = false>
 __device__ __forceinline__ void tile_load2(const Params& p, const int2* queue, int qb, int q, int first, Smem& sm,
                                            Counters& cnt) {
     const int t = threadIdx.x;
@@ -511,7 +527,7 @@ __device__ __forceinline__ void tile_load2(const Params& p, const int2* queue, i
         if (c[u] >= 0) {
             beg[u] = ld_csr<NC>(&p.col_ptr[c[u]]);
             deg[u] = ld_csr<NC>(&p.col_ptr[c[u] + 1]) - beg[u];
-            if (WR) rl[u] = __ldcg(&p.level[rt[u]]);
+            if (WR) rl[u] = SB ? (sb_test(p.srv, rt[u]) ? L0 - 2 : L0) : __ldcg(&p.level[rt[u]]);
         }
     }
     const int off = block_exclusive_scan(deg[0] + deg[1], sm);
@@ -540,7 +556,11 @@ __device__ __forceinline__ void tile_load2(const Params& p, const int2* queue, i
 // the grid barrier's acquire (which makes these loads see the previous
 // levels' and phases' writes): within a level a matched row's column does not
 // change, and a stale "unvisited" level only costs a failed claim.
-template <bool WR, class PushCol, class PushEnd, bool NC = true, bool RV = false, bool CA = false>
+// SB (one-block-per-graph routine, one endpoint per root): a column's claim is
+// setting its bit in p.vis (a shared-memory atomic, no test load, no level
+// write), a root's endpoint claim setting its bit in p.srv; root[] is not
+// written (the queue entries carry the roots).
+template <bool WR, class PushCol, class PushEnd, bool NC = true, bool RV = false, bool CA = false, bool SB = false>
 __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, bool direct, Smem& sm,
                                            Counters& cnt, PushCol push_col, PushEnd push_end, int stamp = 0,
                                            bool use_rv = false) {
@@ -590,7 +610,8 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
                 if (cm[u] >= 0 && !idx_ok(p, cm[u], p.nc)) cm[u] = -3;  // checked build only
 #pragma unroll
             for (int u = 0; u < ILP; ++u)
-                lv[u] = (cm[u] >= 0 && !direct) ? (CA ? __ldca(&p.level[cm[u]]) : __ldcg(&p.level[cm[u]])) : L0 - 1;
+                lv[u] = (SB || cm[u] < 0 || direct) ? L0 - 1
+                                                    : (CA ? __ldca(&p.level[cm[u]]) : __ldcg(&p.level[cm[u]]));
         }
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
@@ -602,7 +623,8 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
                 cnt.em++;
                 // matched row: its column joins the next level unless already reached
                 bool won;
-                if (RV && use_rv) won = lv[u] < stamp;
+                if (SB) won = !sb_test(p.vis, cm[u]) && sb_claim(p.vis, cm[u]);
+                else if (RV && use_rv) won = lv[u] < stamp;
                 else won = lv[u] == L0 - 1 && atomicCAS(&p.level[cm[u]], L0 - 1, lvl + 1) == L0 - 1;
                 if (won) {
                     if (RV) {
@@ -610,14 +632,24 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
                         else __stcg(&p.rvis[r[u]], stamp);
                     }
                     __stcg(&p.pred[r[u]], col);
-                    if (WR) __stcg(&p.root[cm[u]], rt);
+                    if (WR && !SB) __stcg(&p.root[cm[u]], rt);
                     if (RV) __stcg(&p.crec[cm[u]], make_int2(col, r[u]));
                     push_col(make_int2(cm[u], rt));
                 }
             } else if (cm[u] == -1) {
                 // unmatched row: an augmenting path ends here
                 const int row = r[u];
-                if (WR && p.one_ep) {
+                if (SB) {
+                    if (!sb_test(p.srv, rt) && atomicCAS(&p.rmatch[row], -1, -2) == -1) {
+                        if (sb_claim(p.srv, rt)) {
+                            __stcg(&p.pred[row], col);
+                            push_end(row);
+                            sm.has_ep = 1;
+                        } else {
+                            atomicExch(&p.rmatch[row], -1);  // root served meanwhile: give the row back
+                        }
+                    }
+                } else if (WR && p.one_ep) {
                     if (__ldcg(&p.level[rt]) == L0 && atomicCAS(&p.rmatch[row], -1, -2) == -1) {
                         if (atomicCAS(&p.level[rt], L0, -row) == L0) {
                             __stcg(&p.pred[row], col);
@@ -1084,7 +1116,11 @@ __device__ __forceinline__ void block_full_init(const Params& p, Smem& sm, Count
 // block's own writes and atomics keep its SM's L1 coherent, and every launch
 // starts with a clean L1); the serving workers recycle pool memory within one
 // launch and read through L2.
-template <bool WR, bool NC, bool CA = false>
+// SB: one endpoint per root with the graph's tree and served-root marks in
+// the shared-memory bitmaps p.vis / p.srv (at most SB_MAX_COLS columns):
+// cleared at each search's start, the roots' bits set, and the column levels
+// neither tested nor reset.
+template <bool WR, bool NC, bool CA = false, bool SB = false>
 __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters& cnt, int& card_out,
                                  int& phases_out, long long& levels_out, long long& eps_out,
                                  long long& ins_out) {
@@ -1159,6 +1195,14 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
         ++phases;
         // ---- BFS levels; sm.qn is the queue tail, sm.qbase the endpoint count
         if (t == 0) { sm.qn = n_roots; sm.qbase = 0; }
+        if (SB) {
+            for (int w = t; w < (nc + 31) >> 5; w += T) { p.vis[w] = 0u; p.srv[w] = 0u; }
+            __syncthreads();
+            for (int i = t; i < n_roots; i += T) {
+                const int c = __ldcg(&p.queue[i]).x;
+                if (idx_ok(p, c, nc)) atomicOr(&p.vis[c >> 5], 1u << (c & 31));
+            }
+        }
         __syncthreads();
         int qb = 0, qe = n_roots, lvl = L0, levels = 0, n_ep = 0;
         auto push_col = [&](int2 v) { p.queue[atomicAdd(&sm.qn, 1)] = v; };
@@ -1168,10 +1212,10 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
             const bool wide = q > T && 2 * T <= MAX_BLOCK;  // two queue entries per thread
             const int tw = wide ? 2 * T : T;
             for (int first = 0; first < q; first += tw) {
-                if (wide) tile_load2<WR, NC>(p, p.queue, qb, q, first, sm, cnt);
-                else tile_load<WR, NC>(p, p.queue, qb, q, first, T, sm, cnt, nullptr);
-                tile_edges<WR, decltype(push_col), decltype(push_end), NC, false, CA>(p, tw, lvl, q <= T, sm, cnt,
-                                                                           push_col, push_end);
+                if (wide) tile_load2<WR, NC, SB>(p, p.queue, qb, q, first, sm, cnt);
+                else tile_load<WR, NC, SB>(p, p.queue, qb, q, first, T, sm, cnt, nullptr);
+                tile_edges<WR, decltype(push_col), decltype(push_end), NC, false, CA, SB>(p, tw, lvl, q <= T, sm,
+                                                                                     cnt, push_col, push_end);
                 __syncthreads();  // sm.off/beg/col/root are reused by the next tile
             }
             __syncthreads();
@@ -1212,8 +1256,9 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
         __syncthreads();
         if (sm.ok != 0) { status = sm.ok; break; }
         if (incremental) {
-            // columns inserted by this search go back to "unvisited" ...
-            for (int i = n_roots + t; i < tail; i += T) {
+            // columns inserted by this search go back to "unvisited" (SB: the bitmaps are
+            // cleared when the next search starts) ...
+            for (int i = n_roots + t; i < tail && !SB; i += T) {
                 const int c = __ldcg(&p.queue[i]).x;
                 if (!idx_ok(p, c, nc)) continue;
                 __stcg(&p.level[c], L0 - 1);
@@ -1229,7 +1274,7 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
                     c = __ldcg(&p.queue[i]).x;
                     if (!idx_ok(p, c, nc)) c = 0;  // checked build only: recorded, and column 0 is harmless here
                     keep = __ldcg(&p.cmatch[c]) < 0;
-                    if (!keep) {
+                    if (!keep && !SB) {
                         __stcg(&p.level[c], L0 - 1);
                         if (WR) __stcg(&p.root[c], -1);
                     }

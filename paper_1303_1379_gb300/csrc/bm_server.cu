@@ -114,6 +114,7 @@ __device__ __forceinline__ void st_release_sys_s32(int32_t* p, int v) {
 template <bool WR, bool DET = false>
 __global__ void __launch_bounds__(1024, 1) k_serve(ServeParams sp) {
     __shared__ Smem sm;
+    __shared__ unsigned s_vis[bmd::SB_MAX_COLS / 32], s_srv[bmd::SB_MAX_COLS / 32];  // see block_match_graph
     __shared__ long long s_ticket;
     __shared__ SlotDesc s_d;
     Counters cnt{0, 0, 0, 0, 0};
@@ -200,6 +201,11 @@ __global__ void __launch_bounds__(1024, 1) k_serve(ServeParams sp) {
                 p.ekey = (unsigned long long*)(sp.pool + s_d.off_ek);
                 p.ecand = (int32_t*)(sp.pool + s_d.off_ec);
                 status = bmd::block_match_graph_det<false>(p, s_d.greedy, sm, cnt, card, phases, levels, eps, ins);
+            } else if (WR && sp.one_ep && p.nc <= bmd::SB_MAX_COLS) {  // tree marks in shared memory
+                p.vis = s_vis;
+                p.srv = s_srv;
+                status = bmd::block_match_graph<WR, false, false, WR>(p, s_d.greedy, sm, cnt, card, phases, levels,
+                                                                        eps, ins);
             } else {
                 status = bmd::block_match_graph<WR, false>(p, s_d.greedy, sm, cnt, card, phases, levels, eps, ins);
             }
