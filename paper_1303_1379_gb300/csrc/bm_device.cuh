@@ -197,7 +197,8 @@ __device__ __forceinline__ int ld_csr(const int32_t* p) {
 }
 
 // Shared-memory bitmaps of the one-block-per-graph routine (p.vis, p.srv).
-constexpr int SB_MAX_COLS = 65536;  // columns a graph may have for the bitmaps (8 KB each)
+constexpr int SB_MAX_COLS = 61440;  // columns a graph may have for the bitmaps (7.5 KB each; with the
+                                    // shared state the block stays within 48 KB of static shared memory)
 __device__ __forceinline__ bool sb_test(const unsigned* b, int i) {
     return (((const volatile unsigned*)b)[i >> 5] >> (i & 31)) & 1u;
 }
