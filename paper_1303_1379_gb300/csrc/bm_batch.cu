@@ -102,7 +102,12 @@ __global__ void __launch_bounds__(1024, 1) k_batch(BatchParams bp) {
             p.dkey = bp.dkey + co;
             p.ekey = bp.ekey + ro;
             p.ecand = bp.ecand + ro;
-            st = bmd::block_match_graph_det<true>(p, bp.greedy, sm, cnt, card, phases, levels, eps, ins);
+            if (p.nc <= bmd::SB_MAX_COLS) {  // visited marks in shared memory
+                p.vis = s_vis;
+                st = bmd::block_match_graph_det<true, true>(p, bp.greedy, sm, cnt, card, phases, levels, eps, ins);
+            } else {
+                st = bmd::block_match_graph_det<true>(p, bp.greedy, sm, cnt, card, phases, levels, eps, ins);
+            }
         } else if (WR && bp.one_ep && p.nc <= bmd::SB_MAX_COLS) {  // tree marks in shared memory
             p.vis = s_vis;
             p.srv = s_srv;

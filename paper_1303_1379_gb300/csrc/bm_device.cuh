@@ -807,7 +807,9 @@ __device__ __forceinline__ void tile_load_det(const Params& p, const int2* queue
 // tile_edges for the deterministic option (the rules above); lvl is the level
 // of the tile's columns; push_off(r) lists a row that received its first
 // offer of the level in ecand.
-template <class PushCol, class PushOff, bool NC = true>
+// SB (one block per graph): p.vis marks the columns of the trees' levels up
+// to this one; their claim words are not read (their keys cannot change).
+template <class PushCol, class PushOff, bool NC = true, bool SB = false>
 __device__ __forceinline__ void tile_edges_det(const Params& p, int tw, int lvl, Smem& sm, Counters& cnt,
                                                PushCol push_col, PushOff push_off) {
     const int T = blockDim.x;
@@ -841,7 +843,8 @@ __device__ __forceinline__ void tile_edges_det(const Params& p, int tw, int lvl,
         for (int u = 0; u < ILP; ++u)
             if (cm[u] >= 0 && !idx_ok(p, cm[u], p.nc)) cm[u] = -3;  // checked build only
 #pragma unroll
-        for (int u = 0; u < ILP; ++u) key[u] = cm[u] >= 0 ? __ldcg(&p.dkey[cm[u]]) : 0ull;
+        for (int u = 0; u < ILP; ++u)
+            key[u] = (cm[u] < 0 || (SB && sb_test(p.vis, cm[u]))) ? 0ull : __ldcg(&p.dkey[cm[u]]);
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
             if (own[u] < 0) continue;
@@ -1420,7 +1423,9 @@ __device__ __forceinline__ void block_greedy_rounds(const Params& p, Smem& sm) {
 // produced offers -- by the two passes that hand rows to roots.  The search
 // trees are disjoint, so Alternate's walks never meet.  Same outputs as
 // block_match_graph; the result depends on the graph and the start only.
-template <bool NC>
+// SB: p.vis (shared memory, at most SB_MAX_COLS columns) marks the columns of
+// the levels searched so far, so that edges into them skip the claim word.
+template <bool NC, bool SB = false>
 __device__ int block_match_graph_det(const Params& p, int greedy, Smem& sm, Counters& cnt, int& card_out,
                                      int& phases_out, long long& levels_out, long long& eps_out,
                                      long long& ins_out) {
@@ -1456,11 +1461,23 @@ __device__ int block_match_graph_det(const Params& p, int greedy, Smem& sm, Coun
         auto push_col = [&](int2 v) { p.queue[atomicAdd(&sm.qn, 1)] = v; };
         auto push_off = [&](int r) { p.ecand[atomicAdd(&sm.npush, 1)] = r; };
         auto push_end = [&](int r) { p.endpoints[atomicAdd(&sm.qbase, 1)] = r; };
+        if (SB) {  // a new search: no column in a tree yet
+            for (int w = t; w < (nc + 31) >> 5; w += T) p.vis[w] = 0u;
+            __syncthreads();
+        }
         for (;;) {
             const int q = qe - qb;
+            if (SB) {  // the level's own columns join the marked ones before its edges are read
+                for (int i = t; i < q; i += T) {
+                    const int c = __ldcg(&p.queue[qb + i]).x;
+                    if (idx_ok(p, c, nc)) atomicOr(&p.vis[c >> 5], 1u << (c & 31));
+                }
+                __syncthreads();
+            }
             for (int first = 0; first < q; first += T) {
                 tile_load_det<NC>(p, p.queue, qb, q, first, T, lvl, sm, cnt, nullptr);
-                tile_edges_det<decltype(push_col), decltype(push_off), NC>(p, T, lvl, sm, cnt, push_col, push_off);
+                tile_edges_det<decltype(push_col), decltype(push_off), NC, SB>(p, T, lvl, sm, cnt, push_col,
+                                                                            push_off);
                 __syncthreads();  // sm.off/beg/col/root are reused by the next tile
             }
             __syncthreads();

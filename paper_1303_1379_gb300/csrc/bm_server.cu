@@ -200,7 +200,14 @@ __global__ void __launch_bounds__(1024, 1) k_serve(ServeParams sp) {
                 p.dkey = (unsigned long long*)(sp.pool + s_d.off_dk);
                 p.ekey = (unsigned long long*)(sp.pool + s_d.off_ek);
                 p.ecand = (int32_t*)(sp.pool + s_d.off_ec);
-                status = bmd::block_match_graph_det<false>(p, s_d.greedy, sm, cnt, card, phases, levels, eps, ins);
+                if (p.nc <= bmd::SB_MAX_COLS) {  // visited marks in shared memory
+                    p.vis = s_vis;
+                    status = bmd::block_match_graph_det<false, true>(p, s_d.greedy, sm, cnt, card, phases, levels,
+                                                                     eps, ins);
+                } else {
+                    status = bmd::block_match_graph_det<false>(p, s_d.greedy, sm, cnt, card, phases, levels, eps,
+                                                               ins);
+                }
             } else if (WR && sp.one_ep && p.nc <= bmd::SB_MAX_COLS) {  // tree marks in shared memory
                 p.vis = s_vis;
                 p.srv = s_srv;
