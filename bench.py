@@ -18,7 +18,11 @@ ranks), e2e = the same through bm_match_host with pinned host buffers
 (CSR + initial matching up, matching down, inside the timed region),
 roofline = algorithmic bytes of the persistent matching kernel / its
 duration against the measured HBM copy peak, cpu_baseline = the oracle
-(Hopcroft-Karp from the oracle's greedy) on the host cores.
+(Hopcroft-Karp from the oracle's greedy) on the host cores, deterministic =
+the deterministic option from the empty matching with its row-to-column
+array compared (SHA-256 prefix) with the oracle's stored result.  Beside
+the main workload: the mesh and the small uniform graph (workloads), the
+4,096-graph batch (batched) and the served request stream (served).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
        [--workload rmat21|stencil2000|uniform10k]
