@@ -1055,7 +1055,9 @@ __device__ __forceinline__ void step_release_endpoints(const Params& p, int n_ep
 // thread in flight): column half of FixMatching, level / root init, unmatched
 // columns with rows appended to the queue as roots.  Returns the roots in
 // sm.qn; free_total / iso_free get all unmatched columns and those without rows.
-template <bool WR, bool NC>
+// SB: the search keeps its tree marks in the shared-memory bitmaps, so the
+// columns' level and root entries are not written.
+template <bool WR, bool NC, bool SB = false>
 __device__ __forceinline__ void block_full_init(const Params& p, Smem& sm, Counters& cnt, int& free_total,
                                                 int& iso_free) {
     const int T = blockDim.x, t = threadIdx.x, nc = p.nc;
@@ -1079,8 +1081,10 @@ __device__ __forceinline__ void block_full_init(const Params& p, Smem& sm, Count
                 cnt.fixes++;
             }
             const bool is_free = r[u] < 0;
-            __stcg(&p.level[c[u]], is_free ? L0 : L0 - 1);
-            if (WR) __stcg(&p.root[c[u]], is_free ? c[u] : -1);
+            if (!SB) {
+                __stcg(&p.level[c[u]], is_free ? L0 : L0 - 1);
+                if (WR) __stcg(&p.root[c[u]], is_free ? c[u] : -1);
+            }
             if (is_free) {
                 ++nfree;
                 if (ld_csr<NC>(&p.col_ptr[c[u] + 1]) > ld_csr<NC>(&p.col_ptr[c[u]]))
@@ -1132,17 +1136,37 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
     const int t = threadIdx.x;
     const int nr = p.nr, nc = p.nc;
     const bool incremental = WR && p.one_ep;
+    // SB with rows that fit the bitmap: until the search starts, p.vis marks the
+    // rows that are matched, so the cheap matching tests and claims a row in
+    // shared memory instead of loading and CASing its match
+    const bool rows_sb = SB && nr <= SB_MAX_COLS;
     if (t == 0) sm.ok = 0;
     // ---- rows whose column does not point back are unmatched (row half of FixMatching)
-    for (int r = t; r < nr; r += T) {
-        const int m = __ldcg(&p.rmatch[r]);
-        if (m != -1 && (m < 0 || m >= nc || __ldcg(&p.cmatch[m]) != r)) __stcg(&p.rmatch[r], -1);
+    if (rows_sb) {  // a warp takes 32 consecutive rows and writes their bitmap word
+        const int lane = t & 31;
+        for (int r0 = t - lane; r0 < nr; r0 += T) {  // warp-uniform: blockDim is a multiple of 32
+            const int r = r0 + lane;
+            int m = r < nr ? __ldcg(&p.rmatch[r]) : -1;
+            if (m != -1 && (m < 0 || m >= nc || __ldcg(&p.cmatch[m]) != r)) {
+                __stcg(&p.rmatch[r], -1);
+                m = -1;
+            }
+            const unsigned w = __ballot_sync(FULL, m != -1);
+            if (lane == 0) p.vis[r0 >> 5] = w;
+        }
+    } else {
+        for (int r = t; r < nr; r += T) {
+            const int m = __ldcg(&p.rmatch[r]);
+            if (m != -1 && (m < 0 || m >= nc || __ldcg(&p.cmatch[m]) != r)) __stcg(&p.rmatch[r], -1);
+        }
     }
     __syncthreads();
     // ---- cheap matching (Section 4): unmatched columns claim their first free row.
     // A thread walks the lists of 4 columns together, GW rows of each per step,
     // so that 4 x GW row loads and then 4 x GW match loads are in flight at once
     // and a thread takes as long as its longest walk / GW (not the sum of its walks).
+    // rows_sb: a row's test and claim are a bitmap read and atomicOr in shared
+    // memory, and the winner stores both matches (read only after the block barrier).
     if (greedy) {
         constexpr int GW = 4;
         for (int base = 0; base < nc; base += 4 * T) {
@@ -1165,7 +1189,9 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int k = 0; k < GW; ++k) m[u][k] = r[u][k] >= 0 ? ld_volatile(&p.rmatch[r[u][k]]) : 0;
+                    for (int k = 0; k < GW; ++k)
+                        m[u][k] = r[u][k] < 0 ? 0 : rows_sb ? (sb_test(p.vis, r[u][k]) ? 0 : -1)
+                                                            : ld_volatile(&p.rmatch[r[u][k]]);
                 bool more = false;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -1173,7 +1199,9 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
                     bool got = false;
 #pragma unroll
                     for (int k = 0; k < GW; ++k) {  // the first free row of the window, in list order
-                        if (!got && m[u][k] == -1 && atomicCAS(&p.rmatch[r[u][k]], -1, c[u]) == -1) {
+                        if (got || m[u][k] != -1) continue;
+                        if (rows_sb ? sb_claim(p.vis, r[u][k]) : atomicCAS(&p.rmatch[r[u][k]], -1, c[u]) == -1) {
+                            if (rows_sb) p.rmatch[r[u][k]] = c[u];
                             p.cmatch[c[u]] = r[u][k];
                             got = true;
                         }
@@ -1190,7 +1218,7 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
     int phases = 0, card = 0, status = 0;
     long long levels_total = 0, eps_total = 0, ins_total = 0;
     int free_total = 0, iso_free = 0;
-    block_full_init<WR, NC>(p, sm, cnt, free_total, iso_free);
+    block_full_init<WR, NC, SB>(p, sm, cnt, free_total, iso_free);
     int n_roots = sm.qn;
     for (;;) {
         card = nc - free_total;
@@ -1302,7 +1330,7 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
                 }
             }
             __syncthreads();
-            block_full_init<WR, NC>(p, sm, cnt, free_total, iso_free);
+            block_full_init<WR, NC, SB>(p, sm, cnt, free_total, iso_free);
             n_roots = sm.qn;
         }
     }
