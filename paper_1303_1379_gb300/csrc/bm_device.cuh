@@ -53,6 +53,8 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int MAX_BLOCK = 1024;
 constexpr int QBUF = 2048;  // per-block append buffer (entries)
 constexpr int ILP = 4;      // edges per thread in flight
+constexpr int HUB_DEG = 256;  // warp-level expansion: columns of more edges are expanded by the whole block
+constexpr int HUB_MAX = 16;   // ... at most this many per level (the rest stay with their warp)
 constexpr int RV_MAX_Q = 32768;  // largest level (columns) that claims through row stamps
 
 // Control block in device memory, cleared before every launch.  Per-step
@@ -142,6 +144,9 @@ struct Smem {
     int npush;  // columns this block appended during the current step
     int has_ep; // this block appended an endpoint during the current step
     int bc_a, bc_b, bc_c, bc_d, ok;  // barrier broadcast
+    int grab[2];  // warp-level expansion: queue positions handed out, by level parity
+    int nhub[2];  // warp-level expansion: columns set aside for the whole block, by level parity
+    int hub[4][HUB_MAX];  // their column, root, first edge and degree
     int wsum[32];
     int off[MAX_BLOCK];  // exclusive prefix of the tile's degrees
     int beg[MAX_BLOCK];  // first edge of each tile column
@@ -667,6 +672,163 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
                     sm.has_ep = 1;
                 }
             }
+        }
+    }
+}
+
+// Visits edge (col, r) of a column of root rt, r's match being cm, in the
+// one-block-per-graph routine with shared-memory marks (SB): a matched row's
+// column joins the next level if its bit in p.vis was clear (Algorithm 2); an
+// unmatched row ends an augmenting path if the root's bit in p.srv was clear
+// (Algorithm 4, one endpoint per root), the row held by the -2 mark meanwhile.
+template <class PushCol, class PushEnd>
+__device__ __forceinline__ void sb_visit(const Params& p, int col, int rt, int r, int cm, Counters& cnt,
+                                         PushCol push_col, PushEnd push_end) {
+    cnt.edges++;
+    if (cm >= 0) {
+        cnt.em++;
+        if (!sb_test(p.vis, cm) && sb_claim(p.vis, cm)) {
+            __stcg(&p.pred[r], col);
+            push_col(make_int2(cm, rt));
+        }
+    } else if (cm == -1) {
+        if (!sb_test(p.srv, rt) && atomicCAS(&p.rmatch[r], -1, -2) == -1) {
+            if (sb_claim(p.srv, rt)) {
+                __stcg(&p.pred[r], col);
+                push_end(r);
+            } else {
+                atomicExch(&p.rmatch[r], -1);  // root served meanwhile: give the row back
+            }
+        }
+    }
+}
+
+// One BFS level of the one-block-per-graph routine with its tree and served-root
+// marks in the shared-memory bitmaps (SB): the columns of queue positions
+// [qb, qb + q), at level lvl, are expanded by warps, each taking 32 queue
+// entries at a time from the counter *grab (zeroed before the level).  A warp
+// scans its columns' degrees with shuffles and visits their edges 32 x ILP at
+// a time; the column owning edge j is found from which of the warp's columns
+// start at or before j (one OR-reduction of the start positions per 32 edges
+// and a population count per lane), so no per-edge search and no block-wide
+// scan or barrier per tile are needed.  Edges are visited by sb_visit.
+// Columns whose root is already served are skipped whole.  A column of more
+// than HUB_DEG edges is set aside in sm.hub (up to HUB_MAX a level, counted
+// in *nhub) for block_hubs_sb, so that one warp does not walk it alone.  The
+// warp's compacted column records use its 32 slots of sm.beg / sm.col / sm.root.
+template <bool NC, bool CA, class PushCol, class PushEnd>
+__device__ __forceinline__ void warp_expand_sb(const Params& p, int qb, int q, int* grab, int* nhub, Smem& sm,
+                                               Counters& cnt, PushCol push_col, PushEnd push_end) {
+    const int lane = threadIdx.x & 31;
+    const int wb = threadIdx.x & ~31;
+    int* const s_base = &sm.beg[wb];  // beg - start: row_idx position = s_base[k] + j
+    int* const s_col = &sm.col[wb];
+    int* const s_root = &sm.root[wb];
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(grab, 32);
+        g = __shfl_sync(FULL, g, 0);
+        if (g >= q) break;
+        int c = -1, rt = -1, beg = 0, deg = 0;
+        if (g + lane < q) {
+            const int2 ent = __ldcg(&p.queue[qb + g + lane]);
+            c = ent.x;
+            rt = ent.y;
+            if (!idx_ok(p, c, p.nc) || !idx_ok(p, rt, p.nc)) {  // checked build only
+                c = -1;
+            } else {
+                beg = ld_csr<NC>(&p.col_ptr[c]);
+                deg = ld_csr<NC>(&p.col_ptr[c + 1]) - beg;
+                if (sb_test(p.srv, rt)) c = -1;  // Algorithm 4: root already served
+            }
+        }
+        if (c < 0) deg = 0;
+        else cnt.cols++;
+        if (deg > HUB_DEG) {  // the whole block takes it after the warps
+            const int h = atomicAdd(nhub, 1);
+            if (h < HUB_MAX) {
+                sm.hub[0][h] = c;
+                sm.hub[1][h] = rt;
+                sm.hub[2][h] = beg;
+                sm.hub[3][h] = deg;
+                deg = 0;
+            }
+        }
+        int incl = deg;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        const int start = incl - deg;
+        const int rank = __popc(__ballot_sync(FULL, deg > 0) & ((1u << lane) - 1));
+        __syncwarp();  // the previous group's reads of the slots are done
+        if (deg > 0) {
+            s_base[rank] = beg - start;
+            s_col[rank] = c;
+            s_root[rank] = rt;
+        }
+        __syncwarp();
+        int before = 0;  // columns with edges that start before the current 32 edges
+        for (int j0 = 0; j0 < total; j0 += 32 * ILP) {
+            int own[ILP], r[ILP], cm[ILP];
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) {
+                const int J0 = j0 + 32 * u;  // warp-uniform
+                const unsigned starts =
+                    __reduce_or_sync(FULL, (deg > 0 && start >= J0 && start < J0 + 32) ? 1u << (start - J0) : 0u);
+                const int j = J0 + lane;
+                own[u] = -1;
+                r[u] = -1;
+                if (j < total) {
+                    const int k = before + __popc(starts & (0xFFFFFFFFu >> (31 - lane))) - 1;
+                    own[u] = k;
+                    r[u] = ld_csr<NC>(&p.row_idx[s_base[k] + j]);
+                    if (!idx_ok(p, r[u], p.nr)) own[u] = r[u] = -1;
+                }
+                before += __popc(starts);
+            }
+#pragma unroll
+            for (int u = 0; u < ILP; ++u)
+                cm[u] = (own[u] >= 0) ? (CA ? __ldca(&p.rmatch[r[u]]) : __ldcg(&p.rmatch[r[u]])) : -3;
+#pragma unroll
+            for (int u = 0; u < ILP; ++u)
+                if (cm[u] >= 0 && !idx_ok(p, cm[u], p.nc)) cm[u] = -3;  // checked build only
+#pragma unroll
+            for (int u = 0; u < ILP; ++u)
+                if (own[u] >= 0) sb_visit(p, s_col[own[u]], s_root[own[u]], r[u], cm[u], cnt, push_col, push_end);
+        }
+    }
+}
+
+// The columns warp_expand_sb set aside (n of them, n <= HUB_MAX), one after
+// another by the whole block, ILP edges per thread in flight.  A column whose
+// root was served since it was set aside is skipped (Algorithm 4).
+template <bool NC, bool CA, class PushCol, class PushEnd>
+__device__ __forceinline__ void block_hubs_sb(const Params& p, int n, Smem& sm, Counters& cnt, PushCol push_col,
+                                              PushEnd push_end) {
+    const int T = blockDim.x, t = threadIdx.x;
+    for (int h = 0; h < n; ++h) {
+        const int col = sm.hub[0][h], rt = sm.hub[1][h], beg = sm.hub[2][h], deg = sm.hub[3][h];
+        for (int e0 = 0; e0 < deg; e0 += T * ILP) {
+            if (sb_test(p.srv, rt)) break;  // no barrier in this loop: a thread may leave alone
+            int r[ILP], cm[ILP];
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) {
+                const int e = e0 + u * T + t;
+                r[u] = e < deg ? ld_csr<NC>(&p.row_idx[beg + e]) : -1;
+                if (r[u] >= 0 && !idx_ok(p, r[u], p.nr)) r[u] = -1;
+            }
+#pragma unroll
+            for (int u = 0; u < ILP; ++u)
+                cm[u] = r[u] >= 0 ? (CA ? __ldca(&p.rmatch[r[u]]) : __ldcg(&p.rmatch[r[u]])) : -3;
+#pragma unroll
+            for (int u = 0; u < ILP; ++u)
+                if (cm[u] >= 0 && !idx_ok(p, cm[u], p.nc)) cm[u] = -3;  // checked build only
+#pragma unroll
+            for (int u = 0; u < ILP; ++u)
+                if (r[u] >= 0) sb_visit(p, col, rt, r[u], cm[u], cnt, push_col, push_end);
         }
     }
 }
@@ -1226,7 +1388,7 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
         if (phases >= max_phases) { status = -4 /*BM_ERR_ITER_LIMIT*/; break; }
         ++phases;
         // ---- BFS levels; sm.qn is the queue tail, sm.qbase the endpoint count
-        if (t == 0) { sm.qn = n_roots; sm.qbase = 0; }
+        if (t == 0) { sm.qn = n_roots; sm.qbase = 0; sm.grab[0] = 0; sm.nhub[0] = 0; }
         if (SB) {
             for (int w = t; w < (nc + 31) >> 5; w += T) { p.vis[w] = 0u; p.srv[w] = 0u; }
             __syncthreads();
@@ -1243,16 +1405,29 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
             const int q = qe - qb;
             const bool wide = q > T && 2 * T <= MAX_BLOCK;  // two queue entries per thread
             const int tw = wide ? 2 * T : T;
-            for (int first = 0; first < q; first += tw) {
+            int nh = 0;
+            if (SB) {  // by warps; the other counters are zeroed for the next level
+                if (t == 0) { sm.grab[(levels + 1) & 1] = 0; sm.nhub[(levels + 1) & 1] = 0; }
+                warp_expand_sb<NC, CA>(p, qb, q, &sm.grab[levels & 1], &sm.nhub[levels & 1], sm, cnt, push_col,
+                                       push_end);
+                __syncthreads();
+                nh = min(sm.nhub[levels & 1], HUB_MAX);  // block-uniform: reset only after the barrier below
+                if (nh > 0) block_hubs_sb<NC, CA>(p, nh, sm, cnt, push_col, push_end);
+            }
+            for (int first = 0; first < q && !SB; first += tw) {
                 if (wide) tile_load2<WR, NC, SB>(p, p.queue, qb, q, first, sm, cnt);
                 else tile_load<WR, NC, SB>(p, p.queue, qb, q, first, T, sm, cnt, nullptr);
                 tile_edges<WR, decltype(push_col), decltype(push_end), NC, false, CA, SB>(p, tw, lvl, q <= T, sm,
                                                                                      cnt, push_col, push_end);
                 __syncthreads();  // sm.off/beg/col/root are reused by the next tile
             }
-            __syncthreads();
+            if (!SB || nh > 0) __syncthreads();
             const int tail = sm.qn;
             const int eps = sm.qbase;
+            // SB: no barrier precedes the next level's appends (the warps start at
+            // once), so every thread reads the tail, the endpoint count and the hub
+            // count before any warp goes on
+            if (SB) __syncthreads();
             ++levels;
             ins_total += tail - qe;
             if (tail == qe) { n_ep = eps; break; }  // no vertex inserted
