@@ -479,7 +479,7 @@ __device__ __forceinline__ void step_next_roots(const Params& p, const int2* q, 
 // old value, after adding `grab` (a tile index with grab 1 and ctr_base
 // gridDim.x; a queue position with a range width and the end of the static
 // ranges in the guided schedule).  Ends with __syncthreads.
-template <bool WR, bool NC = true, bool SB = false>
+template <bool WR, bool NC = true>
 __device__ __forceinline__ void tile_load(const Params& p, const int2* queue, int qb, int q, int first, int tw,
                                           Smem& sm, Counters& cnt, int32_t* tile_ctr, int grab = 1, int ctr_base = -1) {
     const int t = threadIdx.x;
@@ -494,7 +494,7 @@ __device__ __forceinline__ void tile_load(const Params& p, const int2* queue, in
         } else {
             beg = ld_csr<NC>(&p.col_ptr[c]);
             deg = ld_csr<NC>(&p.col_ptr[c + 1]) - beg;
-            if (WR) rlev = SB ? (sb_test(p.srv, myroot) ? L0 - 2 : L0) : __ldcg(&p.level[myroot]);
+            if (WR) rlev = __ldcg(&p.level[myroot]);
         }
     }
     if (t == 0 && tile_ctr) sm.tile = (ctr_base < 0 ? (int)gridDim.x : ctr_base) + atomicAdd(tile_ctr, grab);
@@ -512,7 +512,7 @@ __device__ __forceinline__ void tile_load(const Params& p, const int2* queue, in
 // <= MAX_BLOCK): the one-block-per-graph routine, where a level's tiles run
 // one after another in one block, gets twice the columns (and their loads)
 // in flight per tile.  Ends with __syncthreads.
-template <bool WR, bool NC = true, bool SB = false>
+template <bool WR, bool NC = true>
 __device__ __forceinline__ void tile_load2(const Params& p, const int2* queue, int qb, int q, int first, Smem& sm,
                                            Counters& cnt) {
     const int t = threadIdx.x;
@@ -533,7 +533,7 @@ __device__ __forceinline__ void tile_load2(const Params& p, const int2* queue, i
         if (c[u] >= 0) {
             beg[u] = ld_csr<NC>(&p.col_ptr[c[u]]);
             deg[u] = ld_csr<NC>(&p.col_ptr[c[u] + 1]) - beg[u];
-            if (WR) rl[u] = SB ? (sb_test(p.srv, rt[u]) ? L0 - 2 : L0) : __ldcg(&p.level[rt[u]]);
+            if (WR) rl[u] = __ldcg(&p.level[rt[u]]);
         }
     }
     const int off = block_exclusive_scan(deg[0] + deg[1], sm);
@@ -562,11 +562,7 @@ __device__ __forceinline__ void tile_load2(const Params& p, const int2* queue, i
 // the grid barrier's acquire (which makes these loads see the previous
 // levels' and phases' writes): within a level a matched row's column does not
 // change, and a stale "unvisited" level only costs a failed claim.
-// SB (one-block-per-graph routine, one endpoint per root): a column's claim is
-// setting its bit in p.vis (a shared-memory atomic, no test load, no level
-// write), a root's endpoint claim setting its bit in p.srv; root[] is not
-// written (the queue entries carry the roots).
-template <bool WR, class PushCol, class PushEnd, bool NC = true, bool RV = false, bool CA = false, bool SB = false>
+template <bool WR, class PushCol, class PushEnd, bool NC = true, bool RV = false, bool CA = false>
 __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, bool direct, Smem& sm,
                                            Counters& cnt, PushCol push_col, PushEnd push_end, int stamp = 0,
                                            bool use_rv = false) {
@@ -616,7 +612,7 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
                 if (cm[u] >= 0 && !idx_ok(p, cm[u], p.nc)) cm[u] = -3;  // checked build only
 #pragma unroll
             for (int u = 0; u < ILP; ++u)
-                lv[u] = (SB || cm[u] < 0 || direct) ? L0 - 1
+                lv[u] = (cm[u] < 0 || direct) ? L0 - 1
                                                     : (CA ? __ldca(&p.level[cm[u]]) : __ldcg(&p.level[cm[u]]));
         }
 #pragma unroll
@@ -629,8 +625,7 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
                 cnt.em++;
                 // matched row: its column joins the next level unless already reached
                 bool won;
-                if (SB) won = !sb_test(p.vis, cm[u]) && sb_claim(p.vis, cm[u]);
-                else if (RV && use_rv) won = lv[u] < stamp;
+                if (RV && use_rv) won = lv[u] < stamp;
                 else won = lv[u] == L0 - 1 && atomicCAS(&p.level[cm[u]], L0 - 1, lvl + 1) == L0 - 1;
                 if (won) {
                     if (RV) {
@@ -638,24 +633,14 @@ __device__ __forceinline__ void tile_edges(const Params& p, int tw, int lvl, boo
                         else __stcg(&p.rvis[r[u]], stamp);
                     }
                     __stcg(&p.pred[r[u]], col);
-                    if (WR && !SB) __stcg(&p.root[cm[u]], rt);
+                    if (WR) __stcg(&p.root[cm[u]], rt);
                     if (RV) __stcg(&p.crec[cm[u]], make_int2(col, r[u]));
                     push_col(make_int2(cm[u], rt));
                 }
             } else if (cm[u] == -1) {
                 // unmatched row: an augmenting path ends here
                 const int row = r[u];
-                if (SB) {
-                    if (!sb_test(p.srv, rt) && atomicCAS(&p.rmatch[row], -1, -2) == -1) {
-                        if (sb_claim(p.srv, rt)) {
-                            __stcg(&p.pred[row], col);
-                            push_end(row);
-                            sm.has_ep = 1;
-                        } else {
-                            atomicExch(&p.rmatch[row], -1);  // root served meanwhile: give the row back
-                        }
-                    }
-                } else if (WR && p.one_ep) {
+                if (WR && p.one_ep) {
                     if (__ldcg(&p.level[rt]) == L0 && atomicCAS(&p.rmatch[row], -1, -2) == -1) {
                         if (atomicCAS(&p.level[rt], L0, -row) == L0) {
                             __stcg(&p.pred[row], col);
@@ -1415,10 +1400,10 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
                 if (nh > 0) block_hubs_sb<NC, CA>(p, nh, sm, cnt, push_col, push_end);
             }
             for (int first = 0; first < q && !SB; first += tw) {
-                if (wide) tile_load2<WR, NC, SB>(p, p.queue, qb, q, first, sm, cnt);
-                else tile_load<WR, NC, SB>(p, p.queue, qb, q, first, T, sm, cnt, nullptr);
-                tile_edges<WR, decltype(push_col), decltype(push_end), NC, false, CA, SB>(p, tw, lvl, q <= T, sm,
-                                                                                     cnt, push_col, push_end);
+                if (wide) tile_load2<WR, NC>(p, p.queue, qb, q, first, sm, cnt);
+                else tile_load<WR, NC>(p, p.queue, qb, q, first, T, sm, cnt, nullptr);
+                tile_edges<WR, decltype(push_col), decltype(push_end), NC, false, CA>(p, tw, lvl, q <= T, sm, cnt,
+                                                                                 push_col, push_end);
                 __syncthreads();  // sm.off/beg/col/root are reused by the next tile
             }
             if (!SB || nh > 0) __syncthreads();
