@@ -1309,39 +1309,43 @@ __device__ int block_match_graph(const Params& p, int greedy, Smem& sm, Counters
     }
     __syncthreads();
     // ---- cheap matching (Section 4): unmatched columns claim their first free row.
-    // A thread walks the lists of 4 columns together, GW rows of each per step,
-    // so that 4 x GW row loads and then 4 x GW match loads are in flight at once
-    // and a thread takes as long as its longest walk / GW (not the sum of its walks).
+    // A thread walks the lists of GU columns together, GW rows of each per step,
+    // so that GU x GW row loads (and, without rows_sb, then GU x GW match loads)
+    // are in flight at once and a thread takes as long as its longest walk / GW
+    // (not the sum of its walks).  A column's row range is loaded beside its match.
     // rows_sb: a row's test and claim are a bitmap read and atomicOr in shared
     // memory, and the winner stores both matches (read only after the block barrier).
     if (greedy) {
-        constexpr int GW = 4;
-        for (int base = 0; base < nc; base += 4 * T) {
-            int c[4], pos[4], e[4];
+        constexpr int GW = 8, GU = 2;
+        for (int base = 0; base < nc; base += GU * T) {
+            int c[GU], pos[GU], e[GU];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < GU; ++u) {
                 c[u] = base + u * T + t;
                 pos[u] = e[u] = 0;
-                if (c[u] < nc && __ldcg(&p.cmatch[c[u]]) == -1) {
+                int m0 = 0;
+                if (c[u] < nc) {  // the row range is loaded beside the match, not after it
+                    m0 = __ldcg(&p.cmatch[c[u]]);
                     pos[u] = ld_csr<NC>(&p.col_ptr[c[u]]);
                     e[u] = ld_csr<NC>(&p.col_ptr[c[u] + 1]);
                 }
+                if (m0 != -1) e[u] = pos[u];
             }
             for (;;) {
-                int r[4][GW], m[4][GW];
+                int r[GU][GW], m[GU][GW];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < GU; ++u)
 #pragma unroll
                     for (int k = 0; k < GW; ++k) r[u][k] = pos[u] + k < e[u] ? ld_csr<NC>(&p.row_idx[pos[u] + k]) : -1;
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < GU; ++u)
 #pragma unroll
                     for (int k = 0; k < GW; ++k)
                         m[u][k] = r[u][k] < 0 ? 0 : rows_sb ? (sb_test(p.vis, r[u][k]) ? 0 : -1)
                                                             : ld_volatile(&p.rmatch[r[u][k]]);
                 bool more = false;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < GU; ++u) {
                     if (pos[u] >= e[u]) continue;
                     bool got = false;
 #pragma unroll
