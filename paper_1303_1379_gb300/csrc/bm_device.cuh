@@ -709,16 +709,25 @@ __device__ __forceinline__ void warp_expand_sb(const Params& p, int qb, int q, i
     int* const s_base = &sm.beg[wb];  // beg - start: row_idx position = s_base[k] + j
     int* const s_col = &sm.col[wb];
     int* const s_root = &sm.root[wb];
+    int g = 0;
+    if (lane == 0) g = atomicAdd(grab, 32);
+    g = __shfl_sync(FULL, g, 0);
+    int2 ent = make_int2(-1, -1);
+    if (g + lane < q) ent = __ldcg(&p.queue[qb + g + lane]);
     for (;;) {
-        int g = 0;
-        if (lane == 0) g = atomicAdd(grab, 32);
-        g = __shfl_sync(FULL, g, 0);
         if (g >= q) break;
         int c = -1, rt = -1, beg = 0, deg = 0;
-        if (g + lane < q) {
-            const int2 ent = __ldcg(&p.queue[qb + g + lane]);
-            c = ent.x;
-            rt = ent.y;
+        const bool mine = g + lane < q;
+        const int2 cur = ent;
+        // the next group's queue entries are loaded while this group is expanded
+        int g2 = 0;
+        if (lane == 0) g2 = atomicAdd(grab, 32);
+        g2 = __shfl_sync(FULL, g2, 0);
+        ent = make_int2(-1, -1);
+        if (g2 + lane < q) ent = __ldcg(&p.queue[qb + g2 + lane]);
+        if (mine) {
+            c = cur.x;
+            rt = cur.y;
             if (!idx_ok(p, c, p.nc) || !idx_ok(p, rt, p.nc)) {  // checked build only
                 c = -1;
             } else {
@@ -784,6 +793,7 @@ __device__ __forceinline__ void warp_expand_sb(const Params& p, int qb, int q, i
             for (int u = 0; u < ILP; ++u)
                 if (own[u] >= 0) sb_visit(p, s_col[own[u]], s_root[own[u]], r[u], cm[u], cnt, push_col, push_end);
         }
+        g = g2;
     }
 }
 
