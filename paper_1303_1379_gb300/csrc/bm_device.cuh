@@ -828,6 +828,124 @@ __device__ __forceinline__ void block_hubs_sb(const Params& p, int n, Smem& sm, 
     }
 }
 
+// warp_expand_sb's walk for any claim rule (the deterministic option's block
+// routine): the columns of queue positions [qb, qb + q) are expanded by warps, each taking 32 queue
+// entries at a time from the counter *grab (zeroed before the level) and
+// loading the next group's entries while it expands the current one.
+// entry(e, c, rt, beg, deg) completes a queue entry into its column, root and
+// row range (c = -1: the column is skipped, e.g. its root is served).  A warp
+// scans its columns' degrees with shuffles and hands their edges out 32 x ILP
+// at a time: the column owning edge j is the last one starting at or before j,
+// found from one OR-reduction of the start positions per 32 edges and a
+// population count per lane, so there is no per-edge search and no block-wide
+// scan or barrier per tile.  round(own, r, s_col, s_root) visits up to ILP
+// edges of the thread (row r[u] of the column s_col[own[u]] of root
+// s_root[own[u]]; own[u] < 0: none).  A column of more than HUB_DEG edges is
+// set aside in sm.hub (up to HUB_MAX a level, counted in *nhub) for
+// block_hubs, so that one warp does not walk it alone.  The warp's compacted
+// column records use its 32 slots of sm.beg / sm.col / sm.root.
+template <bool NC, class Entry, class Round>
+__device__ __forceinline__ void warp_expand(const Params& p, int qb, int q, int* grab, int* nhub, Smem& sm,
+                                            Counters& cnt, Entry entry, Round round) {
+    const int lane = threadIdx.x & 31;
+    const int wb = threadIdx.x & ~31;
+    int* const s_base = &sm.beg[wb];  // beg - start: row_idx position = s_base[k] + j
+    int* const s_col = &sm.col[wb];
+    int* const s_root = &sm.root[wb];
+    int g = 0;
+    if (lane == 0) g = atomicAdd(grab, 32);
+    g = __shfl_sync(FULL, g, 0);
+    int2 ent = make_int2(-1, -1);
+    if (g + lane < q) ent = __ldcg(&p.queue[qb + g + lane]);
+    for (;;) {
+        if (g >= q) break;
+        int c = -1, rt = -1, beg = 0, deg = 0;
+        const bool mine = g + lane < q;
+        const int2 cur = ent;
+        // the next group's queue entries are loaded while this group is expanded
+        int g2 = 0;
+        if (lane == 0) g2 = atomicAdd(grab, 32);
+        g2 = __shfl_sync(FULL, g2, 0);
+        ent = make_int2(-1, -1);
+        if (g2 + lane < q) ent = __ldcg(&p.queue[qb + g2 + lane]);
+        if (mine) entry(cur, c, rt, beg, deg);
+        if (c < 0) deg = 0;
+        else cnt.cols++;
+        if (deg > HUB_DEG) {  // the whole block takes it after the warps
+            const int h = atomicAdd(nhub, 1);
+            if (h < HUB_MAX) {
+                sm.hub[0][h] = c;
+                sm.hub[1][h] = rt;
+                sm.hub[2][h] = beg;
+                sm.hub[3][h] = deg;
+                deg = 0;
+            }
+        }
+        int incl = deg;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        const int start = incl - deg;
+        const int rank = __popc(__ballot_sync(FULL, deg > 0) & ((1u << lane) - 1));
+        __syncwarp();  // the previous group's reads of the slots are done
+        if (deg > 0) {
+            s_base[rank] = beg - start;
+            s_col[rank] = c;
+            s_root[rank] = rt;
+        }
+        __syncwarp();
+        int before = 0;  // columns with edges that start before the current 32 edges
+        for (int j0 = 0; j0 < total; j0 += 32 * ILP) {
+            int own[ILP], r[ILP];
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) {
+                const int J0 = j0 + 32 * u;  // warp-uniform
+                const unsigned starts =
+                    __reduce_or_sync(FULL, (deg > 0 && start >= J0 && start < J0 + 32) ? 1u << (start - J0) : 0u);
+                const int j = J0 + lane;
+                own[u] = -1;
+                r[u] = -1;
+                if (j < total) {
+                    const int k = before + __popc(starts & (0xFFFFFFFFu >> (31 - lane))) - 1;
+                    own[u] = k;
+                    r[u] = ld_csr<NC>(&p.row_idx[s_base[k] + j]);
+                    if (!idx_ok(p, r[u], p.nr)) own[u] = r[u] = -1;
+                }
+                before += __popc(starts);
+            }
+            round(own, r, s_col, s_root);
+        }
+        g = g2;
+    }
+}
+
+// The columns warp_expand set aside (n of them, n <= HUB_MAX), one after
+// another by the whole block, ILP edges per thread in flight; the same
+// round(own, r, s_col, s_root) visits them.  A thread stops a column once
+// alive(root) is false (its root served since it was set aside: Algorithm 4).
+template <bool NC, class Alive, class Round>
+__device__ __forceinline__ void block_hubs(const Params& p, int n, Smem& sm, Alive alive, Round round) {
+    const int T = blockDim.x, t = threadIdx.x;
+    for (int h = 0; h < n; ++h) {
+        const int rt = sm.hub[1][h], beg = sm.hub[2][h], deg = sm.hub[3][h];
+        for (int e0 = 0; e0 < deg; e0 += T * ILP) {
+            if (!alive(rt)) break;  // no barrier in this loop: a thread may leave alone
+            int own[ILP], r[ILP];
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) {
+                const int e = e0 + u * T + t;
+                r[u] = e < deg ? ld_csr<NC>(&p.row_idx[beg + e]) : -1;
+                if (r[u] >= 0 && !idx_ok(p, r[u], p.nr)) r[u] = -1;
+                own[u] = r[u] >= 0 ? 0 : -1;
+            }
+            round(own, r, &sm.hub[0][h], &sm.hub[1][h]);
+        }
+    }
+}
+
 // Expands the queue segment [qb, qe) whose columns are at level lvl, over the
 // whole grid.  New columns are appended at qe + (slot count), endpoints at
 // ep_phase (the phase's running count).  Frontiers of at most one tile per
@@ -964,9 +1082,7 @@ __device__ __forceinline__ void tile_load_det(const Params& p, const int2* queue
 // tile_edges for the deterministic option (the rules above); lvl is the level
 // of the tile's columns; push_off(r) lists a row that received its first
 // offer of the level in ecand.
-// SB (one block per graph): p.vis marks the columns of the trees' levels up
-// to this one; their claim words are not read (their keys cannot change).
-template <class PushCol, class PushOff, bool NC = true, bool SB = false>
+template <class PushCol, class PushOff, bool NC = true>
 __device__ __forceinline__ void tile_edges_det(const Params& p, int tw, int lvl, Smem& sm, Counters& cnt,
                                                PushCol push_col, PushOff push_off) {
     const int T = blockDim.x;
@@ -1001,7 +1117,7 @@ __device__ __forceinline__ void tile_edges_det(const Params& p, int tw, int lvl,
             if (cm[u] >= 0 && !idx_ok(p, cm[u], p.nc)) cm[u] = -3;  // checked build only
 #pragma unroll
         for (int u = 0; u < ILP; ++u)
-            key[u] = (cm[u] < 0 || (SB && sb_test(p.vis, cm[u]))) ? 0ull : __ldcg(&p.dkey[cm[u]]);
+            key[u] = cm[u] < 0 ? 0ull : __ldcg(&p.dkey[cm[u]]);
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
             if (own[u] < 0) continue;
@@ -1657,12 +1773,71 @@ __device__ int block_match_graph_det(const Params& p, int greedy, Smem& sm, Coun
         if (phases >= max_phases) { status = -4 /*BM_ERR_ITER_LIMIT*/; break; }
         ++phases;
         // sm.qn: queue tail; sm.qbase: endpoints; sm.npush: rows listed in ecand this level
-        if (t == 0) { sm.qn = n_roots; sm.qbase = 0; sm.npush = 0; sm.has_ep = 0; }
+        if (t == 0) { sm.qn = n_roots; sm.qbase = 0; sm.npush = 0; sm.has_ep = 0; sm.grab[0] = 0; sm.nhub[0] = 0; }
         __syncthreads();
         int qb = 0, qe = n_roots, lvl = L0, levels = 0, n_ep = 0;
         auto push_col = [&](int2 v) { p.queue[atomicAdd(&sm.qn, 1)] = v; };
         auto push_off = [&](int r) { p.ecand[atomicAdd(&sm.npush, 1)] = r; };
         auto push_end = [&](int r) { p.endpoints[atomicAdd(&sm.qbase, 1)] = r; };
+        // a queue entry of a level after L0 carries no root yet: it is completed from
+        // the column's tree-entry word (as tile_load_det), then the GPUBFS-WR root test
+        auto entry_det = [&](int2 e, int& c, int& rt, int& beg, int& deg) {
+            c = e.x;
+            if (!idx_ok(p, c, nc)) {  // checked build only
+                c = -1;
+                return;
+            }
+            beg = ld_csr<NC>(&p.col_ptr[c]);
+            deg = ld_csr<NC>(&p.col_ptr[c + 1]) - beg;
+            if (lvl == L0) {
+                rt = e.y;  // a root: (c, c)
+            } else {
+                const unsigned long long k = __ldcg(&p.dkey[c]);
+                const int par = (int)(unsigned)(k & 0xffffffffull);
+                const int row = __ldcg(&p.cmatch[c]);
+                if (!idx_ok(p, par, nc) || !idx_ok(p, row, nr)) {
+                    c = -1;
+                    return;
+                }
+                rt = __ldcg(&p.root[par]);
+                __stcg(&p.root[c], rt);
+                __stcg(&p.level[c], lvl);
+                __stcg(&p.pred[row], par);
+                if (p.crec) __stcg(&p.crec[c], make_int2(par, row));
+            }
+            if (!idx_ok(p, rt, nc) || __ldcg(&p.level[rt]) < L0 - 1) c = -1;  // Algorithm 4: root served
+        };
+        // the edges as tile_edges_det: smallest (level, parent) claims a column, smallest
+        // (root, column) an unmatched row's offer
+        auto round_det = [&](const int (&own)[ILP], const int (&r)[ILP], const int* s_col, const int* s_root) {
+            const unsigned long long next_lv = (unsigned long long)(unsigned)(lvl + 1) << 32;
+            int cm[ILP];
+            unsigned long long key[ILP];
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) cm[u] = own[u] >= 0 ? __ldcg(&p.rmatch[r[u]]) : -3;
+#pragma unroll
+            for (int u = 0; u < ILP; ++u)
+                if (cm[u] >= 0 && !idx_ok(p, cm[u], nc)) cm[u] = -3;  // checked build only
+#pragma unroll
+            for (int u = 0; u < ILP; ++u)
+                key[u] = (cm[u] < 0 || (SB && sb_test(p.vis, cm[u]))) ? 0ull : __ldcg(&p.dkey[cm[u]]);
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) {
+                if (own[u] < 0) continue;
+                const int col = s_col[own[u]];
+                cnt.edges++;
+                if (cm[u] >= 0) {
+                    cnt.em++;
+                    // keys only decrease: a stale key that is not above ours is final
+                    const unsigned long long want = next_lv | (unsigned)col;
+                    if (key[u] > want && atomicMin(&p.dkey[cm[u]], want) == DKEY_NONE) push_col(make_int2(cm[u], -1));
+                } else if (cm[u] == -1) {
+                    const unsigned long long want = ((unsigned long long)(unsigned)s_root[own[u]] << 32) | (unsigned)col;
+                    if (atomicMin(&p.ekey[r[u]], want) == DKEY_NONE) push_off(r[u]);
+                }
+            }
+        };
+        auto alive_det = [](int) { return true; };  // a root is served only between levels (det_take)
         if (SB) {  // a new search: no column in a tree yet
             for (int w = t; w < (nc + 31) >> 5; w += T) p.vis[w] = 0u;
             __syncthreads();
@@ -1676,13 +1851,15 @@ __device__ int block_match_graph_det(const Params& p, int greedy, Smem& sm, Coun
                 }
                 __syncthreads();
             }
-            for (int first = 0; first < q; first += T) {
-                tile_load_det<NC>(p, p.queue, qb, q, first, T, lvl, sm, cnt, nullptr);
-                tile_edges_det<decltype(push_col), decltype(push_off), NC, SB>(p, T, lvl, sm, cnt, push_col,
-                                                                            push_off);
-                __syncthreads();  // sm.off/beg/col/root are reused by the next tile
-            }
+            // by warps; the other counters are zeroed for the next level
+            if (t == 0) { sm.grab[(levels + 1) & 1] = 0; sm.nhub[(levels + 1) & 1] = 0; }
+            warp_expand<NC>(p, qb, q, &sm.grab[levels & 1], &sm.nhub[levels & 1], sm, cnt, entry_det, round_det);
             __syncthreads();
+            const int nh = min(sm.nhub[levels & 1], HUB_MAX);  // reset only after the barrier that ends the level
+            if (nh > 0) {
+                block_hubs<NC>(p, nh, sm, alive_det, round_det);
+                __syncthreads();
+            }
             const int n_off = sm.npush;
             const bool found = n_off > 0;
             if (found) {
