@@ -5,7 +5,9 @@ edges expanded by the whole block, more such columns in one level than the
 block sets aside (16), the cheap matching's row claims in shared memory and
 graphs whose rows do not fit them, and the column limit of the bitmaps on
 both sides.  Every graph's |M| equals Hopcroft-Karp's and its matching is
-valid with a Koenig certificate."""
+valid with a Koenig certificate; with the deterministic option (the same
+warp walk with minimum claim rules) the matching and counters equal the
+oracle's."""
 import numpy as np
 import pytest
 
@@ -138,3 +140,39 @@ def test_hub_requests_on_the_serving_workers():
                 assert_maximum(g, rm, cm, info["card"], want[k])
                 srv.release(rid)
         assert srv.stats()["exclusive_runs"] == 0
+
+
+DET_STATS = ("phases", "levels", "endpoints", "inserted", "columns_expanded", "edges_scanned",
+             "edges_to_matched", "alternate_steps")
+
+
+@pytest.mark.parametrize("greedy", [False, True], ids=["empty", "rounds-greedy"])
+def test_hub_columns_deterministic_same_as_the_oracle(greedy):
+    # The deterministic option's block routine expands its levels by the same
+    # warps and hands hubs to the whole block; its minima make the result the
+    # oracle's, matching and counters alike, whatever the warps' order.
+    graphs = hub_set(7)[:10] + [hub_graph(2000, 3 * HUB_MAX, 0, seed=2, base_max=0,
+                                          hub_degs=list(range(HUB_DEG + 1, HUB_DEG + 1 + 3 * HUB_MAX * 20, 20)))]
+    b = batch_of(graphs)
+    R, C = int(b.row_off[-1]), int(b.col_off[-1])
+    w_rm = np.full(R, -1, np.int32)
+    w_cm = np.full(C, -1, np.int32)
+    w_st = dict.fromkeys(DET_STATS, 0)
+    for k, g in enumerate(graphs):
+        rm0 = cm0 = None
+        if greedy:
+            rm0, cm0, _, _ = oracle.greedy_rounds(g.n_rows, g.n_cols, g.col_ptr, g.row_idx)
+        rm, cm, _, st = oracle.apfb_wr_det(g.n_rows, g.n_cols, g.col_ptr, g.row_idx, rm0, cm0)
+        w_rm[b.row_off[k]:b.row_off[k + 1]] = rm
+        w_cm[b.col_off[k]:b.col_off[k + 1]] = cm
+        for key in DET_STATS:
+            w_st[key] += st[key]
+    rm = torch.full((R,), -1, dtype=torch.int32, device="cuda")
+    cm = torch.full((C,), -1, dtype=torch.int32, device="cuda")
+    with bmatch.Batch.from_synth(b, deterministic=1) as bb:
+        rc, st = bb.match(rm, cm, greedy=greedy)
+        status, _ = bb.graph_status()
+    assert rc == 0 and np.all(status == 0)
+    np.testing.assert_array_equal(rm.cpu().numpy(), w_rm)
+    np.testing.assert_array_equal(cm.cpu().numpy(), w_cm)
+    assert {k: st[k] for k in DET_STATS} == w_st
